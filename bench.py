@@ -1,0 +1,384 @@
+"""Benchmark: f-fdot cells/s of the FDAS correlation on GB300, with roofline and CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload survey|small]
+
+A step is one fdas_convolve_power over the whole plane (segment loads, forward FFTs, template
+multiplies, inverse FFTs, overlap discard and power stores: one fused kernel launch).  The
+template bank is built once per plan, outside the timed region, and its time is reported
+separately.  The default workload is the survey-scale plane: 2^22 bins x 201 templates
+(z in [-200, 200] step 2), 512-tap templates, segment length 2048; inputs are seeded synthetic
+spectra (Gaussian noise plus 16 injected chirps).
+
+For N > 1 (torchrun) every rank runs an independent replica on its own GPU (the path has no
+exchange step): value = cells of all ranks / max over ranks of the timed duration.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of this path) on the
+host cores, on a bounded sample of rows of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1711_10855_gb300 import synth  # noqa: E402
+
+METRIC = "f-fdot cells/s on 1 GB300 (2^22 bins x 201 z) and % of HBM roofline"
+UNIT = "cells/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name: str) -> synth.Workload:
+    return synth.survey() if name == "survey" else synth.small()
+
+
+def algorithmic(w: synth.Workload, nseg: int) -> dict:
+    """Per-launch algorithmic bytes and flops (roofline section)."""
+    n, Z, L, m = w.n_bins, w.n_z, w.seg_len, w.tmpl_len
+    V = L - m
+    bytes_plane = 4 * Z * n
+    bytes_spec = 8 * nseg * L          # segments with their m-bin overlap
+    bytes_tmpl = 8 * Z * L + 8 * L     # template spectra + twiddle table
+    logL = int(np.log2(L))
+    fft = 5 * L * logL                 # nominal complex FFT flops
+    flops = nseg * Z * (fft + 6 * L + 3 * V) + nseg * fft
+    return {"bytes": bytes_plane + bytes_spec + bytes_tmpl, "bytes_plane": bytes_plane, "flops": flops}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rows_rate(spec, w: synth.Workload, seconds: float, max_rows: int | None = None):
+    """Time the oracle's row-streamed direct sum on whole rows of the plane, about `seconds` of
+    work: returns (cells/s, rows timed, wall seconds)."""
+    import oracle
+    oracle.build()
+    zs = list(range(w.n_z))
+    rng = np.random.default_rng(5)
+    rng.shuffle(zs)
+    t0 = time.perf_counter()
+    oracle.plane_rows(spec, w.zmax, w.zstep, w.tmpl_len, zs[0], zs[0] + 1)
+    t_row = time.perf_counter() - t0
+    rows = max(1, min(len(zs), int(seconds / max(t_row, 1e-3))))
+    if max_rows:
+        rows = min(rows, max_rows)
+    t0 = time.perf_counter()
+    for zi in zs[:rows]:
+        oracle.plane_rows(spec, w.zmax, w.zstep, w.tmpl_len, zi, zi + 1)
+    dt = time.perf_counter() - t0
+    return rows * w.n_bins / dt, rows, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, one bounded sample of rows per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = workload(args.workload)
+    spec = synth.spectrum(w)
+    cores = cpu_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    rows_per_step = 1
+    rng = np.random.default_rng(17)
+    order = rng.permutation(w.n_z)
+    for i in range(args.warmup):
+        zi = int(order[i % w.n_z])
+        oracle.plane_rows(spec, w.zmax, w.zstep, w.tmpl_len, zi, zi + 1)
+    times = []
+    for i in range(args.steps):
+        zi = int(order[(args.warmup + i) % w.n_z])
+        t0 = time.perf_counter()
+        oracle.plane_rows(spec, w.zmax, w.zstep, w.tmpl_len, zi, zi + rows_per_step)
+        times.append(time.perf_counter() - t0)
+    cells = rows_per_step * w.n_bins
+    value = cells * len(times) / sum(times)
+    sample = f"{rows_per_step} whole row ({cells} cells) of the {w.n_z}x{w.n_bins} plane per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "n_bins": w.n_bins, "n_z": w.n_z,
+                                        "seg_len": w.seg_len, "tmpl_len": w.tmpl_len},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1711_10855_gb300 import fdas
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1711_10855_gb300 import build as fdas_build
+    if rank == 0 or world == 1:
+        fdas_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+        fdas_build.build()
+
+    w = workload(args.workload)
+    # each rank correlates its own spectrum (independent de-dispersion trials)
+    wr = synth.Workload(w.name, w.n_samples, w.zmax, w.zstep, w.tmpl_len, w.seg_len, w.seed + 1000 * rank,
+                        w.chirps)
+    spec = synth.spectrum(wr)
+    plan = fdas.Plan(w.n_bins, w.zmax, w.zstep, w.seg_len, w.tmpl_len)
+    stream = torch.cuda.current_stream(dev)
+    tb0, tb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tb0.record(stream)
+    plan.build_templates(stream)
+    tb1.record(stream)
+    plan.check(stream)
+    template_build_ms = tb0.elapsed_time(tb1)
+
+    d_spec = torch.from_numpy(spec.view(np.float32).copy()).to(dev)
+    plane = torch.empty((plan.n_z, w.n_bins), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        plan.convolve_power(d_spec, plane, stream)
+        flush.fill_(1.0)
+    plan.check(stream)
+
+    # ---- device-timed region: K launches, CUDA events on the launching stream -------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        for e0, e1 in evs:
+            flush.fill_(1.0)                     # L2 flush between timed steps, outside the events
+            e0.record(stream)
+            plan.convolve_power(d_spec, plane, stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+    plan.check(stream)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    t_local = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    cells = plan.n_z * w.n_bins
+    value = cells * args.steps * world / t_max
+
+    # ---- end to end through the public call with host buffers -----------------------------
+    h_spec = torch.from_numpy(spec.view(np.float32).copy()).pin_memory()
+    h_plane = torch.empty((plan.n_z, w.n_bins), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(1):
+        d_spec.copy_(h_spec, non_blocking=True)
+        plan.convolve_power(d_spec, plane, stream)
+        h_plane.copy_(plane, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_spec.copy_(h_spec, non_blocking=True)
+        plan.convolve_power(d_spec, plane, stream)
+        h_plane.copy_(plane, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plan.check(stream)
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = cells * e2e_steps * world / e2e_s
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, peak_src = measured_peaks()
+    alg = algorithmic(w, plan.n_seg)
+    hbm_peak = float(peaks["hbm_gbs"])
+    hbm_achieved = alg["bytes"] / (ms * 1e-3) / 1e9
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2
+    alu_achieved = alg["flops"] / (ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("workload") == w.name and tj.get("kernel_rev") == kernel_rev():
+            traffic = tj.get("dram_bytes_per_launch")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n_bins": w.n_bins, "n_z": plan.n_z, "zmax": w.zmax, "zstep": w.zstep,
+                   "seg_len": w.seg_len, "tmpl_len": w.tmpl_len, "n_seg": plan.n_seg,
+                   "parallelism": f"replicas{world}",
+                   "l2": "512 MiB buffer written between timed steps (outside the step events); "
+                         "each step also writes a 3.4 GB plane"},
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": alu_achieved / alu_peak, "traffic": traffic,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                     "flops_per_launch": alg["flops"]},
+        "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_achieved / hbm_peak, "peak_source": f"hbm_gbs ({peak_src})",
+                         "bytes_per_launch": alg["bytes"]},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(d_spec.numel() * 4),
+                "d2h_bytes_per_step": int(plane.numel() * 4), "steps": e2e_steps},
+        "gpu_launches": args.steps,
+        "template_build_ms": template_build_ms,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    del h_plane, plane, flush
+    torch.cuda.empty_cache()
+    if not args.no_cpu_baseline:
+        cores = cpu_cores()
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        rate, rows, dt = oracle_rows_rate(spec, w, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{rows} whole rows ({rows * w.n_bins} cells) of the plane, "
+                                          f"FP64 direct sum, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_rev() -> str:
+    """Content hash of the kernel sources; ncu traffic figures are valid only for this hash."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("fdas_convolve.cu", "fdas_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1711_10855_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["survey", "small"], default="survey")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * fdas.h -- C ABI of libfdas: the FDAS overlap-and-save correlation on GB300 (sm_103a).
+ *
+ * The library computes the f-fdot power plane of the Fourier Domain Acceleration Search
+ * (Adamek, Dimoudi, Giles & Armour 2017, arXiv 1711.10855):
+ *
+ *   P[z_idx][r] = | sum_{q=-h}^{h} A_{r+q} * conj(Hn_q(z)) |^2          (Section 1, Eq. 2)
+ *
+ * for every bin r in [0, n_bins) and every z = -zmax + z_idx*zstep, z_idx in [0, Z),
+ * Z = 2*zmax/zstep + 1, with A_k = 0 outside [0, n_bins), h = tmpl_len/2, and Hn the
+ * predicted Fourier response of a constant-frequency-derivative signal (Section 1, after
+ * Ransom, Eikenberry & Middleditch 2002), normalised to unit L2 norm over its
+ * tmpl_len + 1 taps q = -h..h:
+ *
+ *   H_q(z) = int_0^1 exp(i*pi*(z*u^2 - (z + 2q)*u)) du,   Hn = H / ||H||_2.
+ *
+ * The garbled lower limit of Eq. 2 is read as r0 - m/2; "m taps" is read as the even span
+ * m = tmpl_len, i.e. m + 1 coefficients q = -m/2..m/2.
+ *
+ * The correlation runs by overlap-and-save (Section 2): segment s holds the L = seg_len
+ * bins A[s*V - h .. s*V - h + L), V = L - tmpl_len; each segment is transformed once, multiplied
+ * by the FFT of every template and transformed back, and the V outputs free of circular
+ * wrap-around are kept.  Transforms follow the DFT sign of Eq. 3 (forward e^{-i2pi nm/N}).
+ *
+ * Conventions for every call:
+ *   - Return value 0 (FDAS_OK) on success, a negative FDAS_ERR_* code otherwise; no C++
+ *     exception crosses the ABI.  fdas_plan_create returns NULL on failure and records the
+ *     code, readable with fdas_last_error() (thread-local).
+ *   - Device pointers are plain CUDA device addresses of the current device, owned by the
+ *     caller unless stated.  Streams are CUDA streams (NULL = legacy default stream).
+ *   - There is no CPU fallback: without a GB300-class device (compute capability 10.3) the
+ *     plan cannot be created (FDAS_ERR_UNSUPPORTED / FDAS_ERR_NO_DEVICE).
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdas_plan fdas_plan;          /* opaque plan: sizes, template bank, workspace */
+typedef struct CUstream_st* fdas_stream_t;   /* identical to cudaStream_t */
+
+enum fdas_status {
+  FDAS_OK = 0,
+  FDAS_ERR_INVALID = -1,      /* an argument is out of its documented range */
+  FDAS_ERR_ALIGN = -2,        /* a pointer does not have the documented alignment */
+  FDAS_ERR_NOT_BUILT = -3,    /* fdas_convolve_power before fdas_templates_build */
+  FDAS_ERR_ALLOC = -4,        /* device allocation failed */
+  FDAS_ERR_CUDA = -5,         /* a CUDA runtime call or kernel launch failed */
+  FDAS_ERR_NO_DEVICE = -6,    /* no CUDA device is visible */
+  FDAS_ERR_UNSUPPORTED = -7,  /* the current device is not compute capability 10.3 */
+  FDAS_ERR_TIMEOUT = -8       /* a bounded device-side wait gave up (see fdas_check) */
+};
+
+/* Limits checked by fdas_plan_create. */
+#define FDAS_MIN_SEG_LEN 256
+#define FDAS_MAX_SEG_LEN 2048
+
+/*
+ * Create a plan for an n_bins-bin spectrum, the z grid -zmax..zmax step zstep, segment
+ * length seg_len and template span tmpl_len (Section 1, Eq. 2; Section 2 overlap-and-save).
+ *
+ *   n_bins    >= 4 and a multiple of 4, < 2^32.
+ *   zmax      >= 0, zstep >= 1, zmax % zstep == 0; Z = 2*zmax/zstep + 1 <= 65535.
+ *   seg_len   L, a power of two in [FDAS_MIN_SEG_LEN, FDAS_MAX_SEG_LEN].
+ *   tmpl_len  m, a multiple of 4 with 4 <= m <= L/2 (so V = L - m >= L/2, V % 4 == 0).
+ *
+ * Host call.  Validates the arguments before touching the device, then allocates the plan's
+ * device memory on the current device: the template bank (Z*L complex64), the FP64 taps
+ * (Z*(m+1) complex128), a twiddle table (L complex64) and a status word.  Returns NULL on
+ * failure with fdas_last_error() set to FDAS_ERR_INVALID, FDAS_ERR_NO_DEVICE,
+ * FDAS_ERR_UNSUPPORTED, FDAS_ERR_ALLOC or FDAS_ERR_CUDA.  The plan is used only on the device
+ * that was current at creation.
+ */
+fdas_plan* fdas_plan_create(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len);
+
+/* Code of the last failed fdas_plan_create on this thread (FDAS_OK if none). */
+int fdas_last_error(void);
+
+/* Static, NUL-terminated description of a status code. */
+const char* fdas_error_string(int code);
+
+/*
+ * Build the template bank on the GPU (stream-ordered, asynchronous): for every z_idx the taps
+ * H_q(z), q = -h..h, are computed in FP64 (composite Gauss-Legendre quadrature of the response
+ * integral), normalised to unit L2 norm (the "predicted, normalized Fourier response" of
+ * Section 1), conjugated, placed circularly so that the valid outputs of a segment are its
+ * first V bins, transformed by an FP64 DFT of length L (1/L folded in) and stored as complex64.
+ * Must complete before fdas_convolve_power (same stream, or synchronise).  Returns FDAS_OK,
+ * FDAS_ERR_INVALID (NULL plan) or FDAS_ERR_CUDA.
+ */
+int fdas_templates_build(fdas_plan* plan, fdas_stream_t stream);
+
+/*
+ * The hot path (Eq. 2 by overlap-and-save, Section 2): one fused kernel launch on `stream`.
+ *
+ *   d_spectrum  n_bins complex64 values (interleaved re, im floats), device memory, 16-byte
+ *               aligned, read-only, caller-owned.
+ *   d_plane     Z x n_bins float32, row-major (row z_idx = (z + zmax)/zstep, pitch n_bins),
+ *               device memory, 16-byte aligned, caller-owned; every element is overwritten.
+ *
+ * Asynchronous: no host synchronisation and no allocation.  Returns FDAS_ERR_NOT_BUILT before
+ * fdas_templates_build, FDAS_ERR_INVALID for NULL pointers, FDAS_ERR_ALIGN for misaligned
+ * pointers, FDAS_ERR_CUDA if the launch fails.  Calls on one plan from different streams must
+ * not overlap (they share the plan's status word).  A device-side bounded wait that gives up
+ * is reported by the next fdas_check().
+ */
+int fdas_convolve_power(fdas_plan* plan, const float* d_spectrum, float* d_plane,
+                        fdas_stream_t stream);
+
+/*
+ * Synchronise `stream` and report the plan's device status word: FDAS_OK, or FDAS_ERR_TIMEOUT
+ * if a kernel of this plan abandoned a bounded wait (its outputs are then unspecified); the
+ * word is cleared.  FDAS_ERR_CUDA if the synchronisation itself fails.
+ */
+int fdas_check(fdas_plan* plan, fdas_stream_t stream);
+
+/* Free the plan's device memory (synchronises the device first).  NULL is a no-op. */
+int fdas_destroy(fdas_plan* plan);
+
+/* Plan sizes: Z templates, V valid outputs per segment, nseg = ceil(n_bins / V) segments.
+ * Any output pointer may be NULL. */
+int fdas_plan_dims(const fdas_plan* plan, int* Z, int* V, int64_t* nseg);
+
+/*
+ * Introspection for tests (synchronising copies, not for the hot path).
+ * fdas_template_taps: the normalised FP64 taps Hn_q(z) of row z_idx, q = -h..h, as 2*(m+1)
+ *   doubles (re, im) into host memory.
+ * fdas_template_spectrum: the stored complex64 template spectrum of row z_idx in natural
+ *   order k = 0..L-1 (2*L floats into host memory): T[k] = (1/L) sum_q conj(Hn_q) e^{+i2pi k(q+h)/L}.
+ * Both return FDAS_ERR_NOT_BUILT before fdas_templates_build and FDAS_ERR_INVALID for a bad
+ * z_idx or NULL pointer.
+ */
+int fdas_template_taps(fdas_plan* plan, int z_idx, double* host_out);
+int fdas_template_spectrum(fdas_plan* plan, int z_idx, float* host_out);
+
+/*
+ * Steps a2 + a3 alone, for tests of the in-kernel FFT: the forward FFT (Eq. 3 sign) of every
+ * overlap-and-save segment, X_s[k] = sum_i A[s*V - h + i] e^{-i2pi ik/L} (zeros outside
+ * [0, n_bins)), written in natural order to d_out (nseg x L complex64, interleaved floats,
+ * device memory, 16-byte aligned, caller-owned).  Asynchronous on `stream`.
+ */
+int fdas_segment_spectra(fdas_plan* plan, const float* d_spectrum, float* d_out,
+                         fdas_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

@@ -147,3 +147,26 @@ def plane_samples(spectrum: np.ndarray, zmax: int, zstep: int, m: int,
     if rc != 0:
         raise ValueError(f"oracle_plane_samples failed ({rc})")
     return out
+
+
+def segment_spectra(spectrum: np.ndarray, seg_len: int, m: int) -> np.ndarray:
+    """Forward DFT (Eq. 3 sign, FP64) of every overlap-and-save segment: row s is
+    X_s[k] = sum_i A[s*V - h + i] exp(-i 2 pi i k / L), A = 0 outside [0, n), V = L - m, h = m/2.
+    Library FFT as the DFT step (Section 2's segmentation, Eq. 3)."""
+    A = np.asarray(spectrum).astype(np.complex128)
+    n, L, h = A.size, seg_len, m // 2
+    V = L - m
+    nseg = -(-n // V)
+    padded = np.zeros(nseg * V + L, dtype=np.complex128)
+    padded[h:h + n] = A
+    segs = np.stack([padded[s * V:s * V + L] for s in range(nseg)])
+    return np.fft.fft(segs, axis=1)
+
+
+def template_spectrum(z: int, m: int, seg_len: int) -> np.ndarray:
+    """T_z[k] = (1/L) sum_{q=-h}^{h} conj(Hn_q(z)) exp(+i 2 pi k (q + h) / L), FP64: the
+    conjugated, normalised template placed at circular index q + h and transformed, with the
+    inverse transform's 1/L folded in (Section 2: Fourier-domain convolution per segment)."""
+    g = np.zeros(seg_len, dtype=np.complex128)
+    g[:m + 1] = np.conj(template(z, m))
+    return np.fft.ifft(g)

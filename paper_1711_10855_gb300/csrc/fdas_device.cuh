@@ -1,0 +1,237 @@
+// fdas_device.cuh -- device building blocks of the fused FDAS kernel (sm_103a).
+//
+//  * compile-time twiddle factors (cos/sin of 2*pi*j/M from a Taylor series on [0, pi/4]),
+//  * an in-register radix-2 decimation-in-time FFT whose butterflies are written as fused
+//    multiply-adds (the rotation w*b is c*(b + i*t*b) with t = tan or cot of the angle, so a
+//    butterfly with a non-trivial twiddle is 6 FMAs and one with w in {1, +-i} is 4 adds),
+//  * mbarrier / bulk-copy (TMA) wrappers whose waits are bounded in time.
+//
+// The DFT sign follows Eq. 3 of Adamek et al. 2017: forward X_m = sum_n x_n e^{-i2pi nm/N}
+// (SIGN = -1); the inverse transform used after the template multiply has SIGN = +1 and no
+// 1/N (the 1/L is folded into the stored template spectra).
+#pragma once
+
+#include <cstdint>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+namespace fdas {
+
+// ---------------------------------------------------------------------------------------
+// Compile-time trigonometry
+// ---------------------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+__host__ __device__ constexpr double taylor_sin(double x) {   // |x| <= pi/4
+  double x2 = x * x, term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / (double)((2 * k) * (2 * k + 1));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {   // |x| <= pi/4
+  double x2 = x * x, term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / (double)((2 * k - 1) * (2 * k));
+    sum += term;
+  }
+  return sum;
+}
+
+struct CosSin {
+  double c, s;
+};
+
+// cos and sin of 2*pi*j/M for integer j and M a power of two, with the quadrant and the
+// octant reduced exactly in integers.
+__host__ __device__ constexpr CosSin cossin_2pi(long long j, long long M) {
+  j %= M;
+  if (j < 0) j += M;
+  if (M == 1) return {1.0, 0.0};
+  if (M == 2) return j == 0 ? CosSin{1.0, 0.0} : CosSin{-1.0, 0.0};
+  const long long q = (4 * j) / M;        // quadrant
+  const long long r = 4 * j - q * M;      // angle within the quadrant = (pi/2) * r / M
+  double c = 0.0, s = 0.0;
+  if (2 * r <= M) {
+    const double phi = (kPi / 2.0) * (double)r / (double)M;
+    c = taylor_cos(phi);
+    s = taylor_sin(phi);
+  } else {
+    const double phi = (kPi / 2.0) * (double)(M - r) / (double)M;
+    c = taylor_sin(phi);
+    s = taylor_cos(phi);
+  }
+  switch (q) {
+    case 0: return {c, s};
+    case 1: return {-s, c};
+    case 2: return {-c, -s};
+    default: return {s, -c};
+  }
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+__host__ __device__ constexpr double cabsd(double x) { return x < 0 ? -x : x; }
+
+// ---------------------------------------------------------------------------------------
+// Compile-time loops
+// ---------------------------------------------------------------------------------------
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ---------------------------------------------------------------------------------------
+// Complex helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_conj_b(float2 a, float2 b) {   // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float power(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// ---------------------------------------------------------------------------------------
+// Radix-2 DIT butterfly a' = a + w b, b' = a - w b with w = exp(SIGN * i * 2*pi*J/M)
+// ---------------------------------------------------------------------------------------
+template <int J, int M, int SIGN>
+__device__ __forceinline__ void butterfly(float2& a, float2& b) {
+  constexpr CosSin cs = cossin_2pi(J, M);
+  constexpr double wc = cs.c;
+  constexpr double ws = SIGN * cs.s;
+  if constexpr (J == 0) {
+    const float2 t = a;
+    a = make_float2(t.x + b.x, t.y + b.y);
+    b = make_float2(t.x - b.x, t.y - b.y);
+  } else if constexpr (4 * J == M) {
+    // w = SIGN * i:  w*b = SIGN * (-b.y, b.x)
+    const float2 t = a;
+    if constexpr (SIGN > 0) {
+      a = make_float2(t.x - b.y, t.y + b.x);
+      b = make_float2(t.x + b.y, t.y - b.x);
+    } else {
+      a = make_float2(t.x + b.y, t.y - b.x);
+      b = make_float2(t.x - b.y, t.y + b.x);
+    }
+  } else if constexpr (cabsd(wc) >= cabsd(ws)) {
+    // w*b = c * (b.x - t b.y, b.y + t b.x), t = tan
+    constexpr float t = (float)(ws / wc);
+    constexpr float c = (float)wc;
+    const float ur = fmaf(-t, b.y, b.x);
+    const float ui = fmaf(t, b.x, b.y);
+    const float2 s = a;
+    a = make_float2(fmaf(c, ur, s.x), fmaf(c, ui, s.y));
+    b = make_float2(fmaf(-c, ur, s.x), fmaf(-c, ui, s.y));
+  } else {
+    // w*b = s * (ct b.x - b.y, ct b.y + b.x), ct = cot
+    constexpr float ct = (float)(wc / ws);
+    constexpr float sn = (float)ws;
+    const float ur = fmaf(ct, b.x, -b.y);
+    const float ui = fmaf(ct, b.y, b.x);
+    const float2 s = a;
+    a = make_float2(fmaf(sn, ur, s.x), fmaf(sn, ui, s.y));
+    b = make_float2(fmaf(-sn, ur, s.x), fmaf(-sn, ui, s.y));
+  }
+}
+
+template <int N, int SIGN, int S, int I>
+__device__ __forceinline__ void stage_butterfly(float2 (&v)[N]) {
+  constexpr int span = 1 << S;
+  constexpr int blk = (I / span) * (2 * span);
+  constexpr int j = I % span;
+  butterfly<j, 2 * span, SIGN>(v[blk + j], v[blk + j + span]);
+}
+template <int N, int SIGN, int S, int... I>
+__device__ __forceinline__ void fft_stage(float2 (&v)[N], std::integer_sequence<int, I...>) {
+  (stage_butterfly<N, SIGN, S, I>(v), ...);
+}
+template <int N, int SIGN, int... S>
+__device__ __forceinline__ void fft_stages(float2 (&v)[N], std::integer_sequence<int, S...>) {
+  (fft_stage<N, SIGN, S>(v, std::make_integer_sequence<int, N / 2>{}), ...);
+}
+
+// In-register DFT of N points: on entry v[i] = x[bitrev(i)], on exit v[m] = X[m] =
+// sum_n x[n] exp(SIGN * i * 2*pi*n*m/N)  (Eq. 3 for SIGN = -1).
+template <int N, int SIGN>
+__device__ __forceinline__ void fft_dit(float2 (&v)[N]) {
+  fft_stages<N, SIGN>(v, std::make_integer_sequence<int, ilog2(N)>{});
+}
+
+// ---------------------------------------------------------------------------------------
+// mbarrier and bulk asynchronous copies (TMA), with time-bounded waits
+// ---------------------------------------------------------------------------------------
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity to complete; false if kWaitLimitNs elapsed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// 1-D bulk copy global -> shared, completion counted in bytes on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// 1-D tiled tensor copy global -> shared of one box starting at element x (may be negative or
+// beyond the extent: those elements are zero-filled).  x * element size must be a multiple of
+// 16 bytes.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* tmap, int32_t x, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], "
+      "[%3];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(smem_u32(bar))
+      : "memory");
+}
+
+}  // namespace fdas

@@ -1,0 +1,165 @@
+"""ctypes binding of libfdas (include/fdas.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module converts torch
+tensors / integers into pointers and sizes, passes the current CUDA stream, and raises
+``FdasError`` for non-zero status codes.  There is no fallback: if ``libfdas.so`` is absent
+the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfdas.so")
+
+FDAS_OK = 0
+ERRORS = {
+    -1: "FDAS_ERR_INVALID", -2: "FDAS_ERR_ALIGN", -3: "FDAS_ERR_NOT_BUILT", -4: "FDAS_ERR_ALLOC",
+    -5: "FDAS_ERR_CUDA", -6: "FDAS_ERR_NO_DEVICE", -7: "FDAS_ERR_UNSUPPORTED", -8: "FDAS_ERR_TIMEOUT",
+}
+EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_templates_build",
+            "fdas_convolve_power", "fdas_check", "fdas_destroy", "fdas_plan_dims",
+            "fdas_template_taps", "fdas_template_spectrum", "fdas_segment_spectra"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FdasError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({error_string(code)})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree libfdas.so (built by paper_1711_10855_gb300.build / __graft_entry__.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FileNotFoundError(f"{LIB_PATH} is missing: run `python -m paper_1711_10855_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            L.fdas_plan_create.argtypes = [i64, i32, i32, i32, i32]
+            L.fdas_plan_create.restype = vp
+            L.fdas_last_error.argtypes = []
+            L.fdas_last_error.restype = i32
+            L.fdas_error_string.argtypes = [i32]
+            L.fdas_error_string.restype = ctypes.c_char_p
+            L.fdas_templates_build.argtypes = [vp, vp]
+            L.fdas_templates_build.restype = i32
+            L.fdas_convolve_power.argtypes = [vp, vp, vp, vp]
+            L.fdas_convolve_power.restype = i32
+            L.fdas_check.argtypes = [vp, vp]
+            L.fdas_check.restype = i32
+            L.fdas_destroy.argtypes = [vp]
+            L.fdas_destroy.restype = i32
+            L.fdas_plan_dims.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
+            L.fdas_plan_dims.restype = i32
+            L.fdas_template_taps.argtypes = [vp, i32, vp]
+            L.fdas_template_taps.restype = i32
+            L.fdas_template_spectrum.argtypes = [vp, i32, vp]
+            L.fdas_template_spectrum.restype = i32
+            L.fdas_segment_spectra.argtypes = [vp, vp, vp, vp]
+            L.fdas_segment_spectra.restype = i32
+            _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().fdas_error_string(int(code)).decode()
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor (or an integer address passed through)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer of {type(x)!r}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != FDAS_OK:
+        raise FdasError(rc, what)
+
+
+class Plan:
+    """One fdas_plan: (n_bins, zmax, zstep, seg_len, tmpl_len) and its device template bank."""
+
+    def __init__(self, n_bins: int, zmax: int, zstep: int, seg_len: int, tmpl_len: int):
+        L = lib()
+        h = L.fdas_plan_create(int(n_bins), int(zmax), int(zstep), int(seg_len), int(tmpl_len))
+        if not h:
+            raise FdasError(L.fdas_last_error(), "fdas_plan_create")
+        self._h = h
+        self.n_bins, self.zmax, self.zstep = int(n_bins), int(zmax), int(zstep)
+        self.seg_len, self.tmpl_len = int(seg_len), int(tmpl_len)
+        Z, V, nseg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(L.fdas_plan_dims(h, ctypes.byref(Z), ctypes.byref(V), ctypes.byref(nseg)), "fdas_plan_dims")
+        self.n_z, self.valid, self.n_seg = Z.value, V.value, nseg.value
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def build_templates(self, stream=None):
+        _check(lib().fdas_templates_build(self._h, _stream(stream)), "fdas_templates_build")
+
+    def convolve_power(self, spectrum, plane, stream=None):
+        """Async: plane (Z x n_bins float32) <- |correlation|^2 of spectrum (n_bins complex64)."""
+        _check(lib().fdas_convolve_power(self._h, _ptr(spectrum), _ptr(plane), _stream(stream)),
+               "fdas_convolve_power")
+
+    def segment_spectra(self, spectrum, out, stream=None):
+        _check(lib().fdas_segment_spectra(self._h, _ptr(spectrum), _ptr(out), _stream(stream)),
+               "fdas_segment_spectra")
+
+    def check(self, stream=None):
+        _check(lib().fdas_check(self._h, _stream(stream)), "fdas_check")
+
+    def template_taps(self, z_idx: int) -> np.ndarray:
+        out = np.empty(2 * (self.tmpl_len + 1), dtype=np.float64)
+        _check(lib().fdas_template_taps(self._h, int(z_idx), out.ctypes.data), "fdas_template_taps")
+        return out.view(np.complex128)
+
+    def template_spectrum(self, z_idx: int) -> np.ndarray:
+        out = np.empty(2 * self.seg_len, dtype=np.float32)
+        _check(lib().fdas_template_spectrum(self._h, int(z_idx), out.ctypes.data), "fdas_template_spectrum")
+        return out.view(np.complex64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fdas_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plane_shape(plan: Plan) -> tuple[int, int]:
+    return plan.n_z, plan.n_bins

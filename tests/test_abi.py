@@ -1,0 +1,87 @@
+"""The C ABI without a GPU: the library loads, exports every function include/fdas.h declares,
+and the host-side argument validation of fdas_plan_create / NULL handling works."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1711_10855_gb300 import build as fdas_build
+from paper_1711_10855_gb300 import fdas
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fdas_build.build()
+    return fdas.lib()
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(fdas_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fdas_plan_create", "fdas_templates_build", "fdas_convolve_power", "fdas_destroy"):
+        assert required in names
+    assert set(fdas.EXPORTED) <= set(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_error_strings(lib):
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
+        assert len(fdas.error_string(code)) > 0
+    assert fdas.error_string(12345) == "unknown fdas status"
+
+
+@pytest.mark.parametrize("args", [
+    (0, 20, 2, 512, 64),        # n_bins < 4
+    (1002, 20, 2, 512, 64),     # n_bins % 4
+    ((1 << 30) + 4, 0, 1, 512, 64),
+    (4096, 21, 2, 512, 64),     # zmax % zstep
+    (4096, 20, 0, 512, 64),     # zstep < 1
+    (4096, -2, 2, 512, 64),     # zmax < 0
+    (4096, 200000, 1, 512, 64), # Z > 65535
+    (4096, 20, 2, 500, 64),     # not a power of two
+    (4096, 20, 2, 128, 64),     # below the minimum segment
+    (4096, 20, 2, 8192, 64),    # above the maximum segment
+    (4096, 20, 2, 512, 2),      # m < 4
+    (4096, 20, 2, 512, 66),     # m % 4
+    (4096, 20, 2, 512, 260),    # m > L/2
+])
+def test_plan_create_rejects_invalid_arguments(lib, args):
+    lib.fdas_plan_create.restype = ctypes.c_void_p
+    h = lib.fdas_plan_create(ctypes.c_int64(args[0]), *args[1:])
+    assert not h
+    assert lib.fdas_last_error() == -1
+
+
+def test_null_plan_calls(lib):
+    assert lib.fdas_destroy(None) == 0
+    assert lib.fdas_templates_build(None, None) == -1
+    assert lib.fdas_convolve_power(None, None, None, None) == -1
+    assert lib.fdas_check(None, None) == -1
+    assert lib.fdas_plan_dims(None, None, None, None) == -1
+    assert lib.fdas_template_taps(None, 0, None) == -1
+    assert lib.fdas_template_spectrum(None, 0, None) == -1
+    assert lib.fdas_segment_spectra(None, None, None, None) == -1
+
+
+def test_no_device_is_an_error_not_a_fallback(lib, cuda_available):
+    if cuda_available:
+        pytest.skip("a GPU is present")
+    h = lib.fdas_plan_create(ctypes.c_int64(4096), 20, 2, 512, 64)
+    assert not h
+    assert lib.fdas_last_error() in (-6, -5)

@@ -97,3 +97,34 @@ def test_small_workload_peak_and_noise_mean():
     far = np.r_[0:15000, 25000:w.n_bins]
     row_means = P[:, far].mean(axis=1)
     assert np.all(np.abs(row_means / N - 1.0) < 0.06)
+
+
+def test_segment_spectra_definition():
+    """Rows of oracle.segment_spectra against an explicit DFT-matrix sum over the zero-padded
+    segment window A[s*V - h + i]."""
+    rng = np.random.default_rng(8)
+    n, L, m = 300, 32, 8
+    A = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    X = oracle.segment_spectra(A, L, m)
+    V, h = L - m, m // 2
+    assert X.shape == (-(-n // V), L)
+    W = np.exp(-2j * np.pi * np.outer(np.arange(L), np.arange(L)) / L)
+    for s in range(X.shape[0]):
+        seg = np.array([A[s * V - h + i] if 0 <= s * V - h + i < n else 0 for i in range(L)], complex)
+        np.testing.assert_allclose(X[s], W @ seg, rtol=0, atol=1e-11)
+
+
+def test_template_spectrum_gives_the_correlation():
+    """IDFT(segment spectrum * template spectrum) reproduces Eq. 2's direct sum on the first V
+    outputs of every segment (the overlap-and-save identity the GPU path relies on)."""
+    rng = np.random.default_rng(9)
+    n, L, m, z = 500, 64, 16, 6
+    A = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    X = oracle.segment_spectra(A, L, m)
+    T = oracle.template_spectrum(z, m, L)
+    W = np.exp(2j * np.pi * np.outer(np.arange(L), np.arange(L)) / L)   # inverse DFT without 1/L
+    y = (W @ (X * T[None, :]).T).T
+    V = L - m
+    P = np.abs(y[:, :V]).reshape(-1)[:n] ** 2
+    ref = oracle.plane_rows(A, z, z, m, row0=2, row1=3)[0]   # zmax = zstep = z: rows -z, 0, +z
+    np.testing.assert_allclose(P, ref, rtol=0, atol=1e-11 * ref.max())
