@@ -50,8 +50,14 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name: str) -> synth.Workload:
-    return synth.survey() if name == "survey" else synth.small()
+def workload(name: str, n_bins: int | None = None) -> synth.Workload:
+    w = synth.survey() if name == "survey" else synth.small()
+    if n_bins:
+        # same z grid, template span and segment length on a shorter noise-only spectrum
+        # (used for profiling captures, not for bench lines)
+        w = synth.Workload(f"{w.name}-n{n_bins}", 2 * n_bins, w.zmax, w.zstep, w.tmpl_len, w.seg_len,
+                           w.seed, ())
+    return w
 
 
 def algorithmic(w: synth.Workload, nseg: int) -> dict:
@@ -165,7 +171,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    w = workload(args.workload)
+    w = workload(args.workload, args.n_bins)
     spec = synth.spectrum(w)
     cores = cpu_cores()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
@@ -214,7 +220,7 @@ def run_ours(args):
         torch.distributed.barrier()
         fdas_build.build()
 
-    w = workload(args.workload)
+    w = workload(args.workload, args.n_bins)
     # each rank correlates its own spectrum (independent de-dispersion trials)
     wr = synth.Workload(w.name, w.n_samples, w.zmax, w.zstep, w.tmpl_len, w.seg_len, w.seed + 1000 * rank,
                         w.chirps)
@@ -372,6 +378,7 @@ def main():
     ap.add_argument("--workload", choices=["survey", "small"], default="survey")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-bins", type=int, default=None, help="profiling only: shorter spectrum, same geometry")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
