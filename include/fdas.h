@@ -146,6 +146,42 @@ int fdas_template_spectrum(fdas_plan* plan, int z_idx, float* host_out);
 int fdas_segment_spectra(fdas_plan* plan, const float* d_spectrum, float* d_out,
                          fdas_stream_t stream);
 
+/*
+ * Allocation-free variant of fdas_convolve_power, for callers that cannot allocate device
+ * memory: code on a latency-critical path where cudaMalloc may synchronise the device and take
+ * unbounded time, components whose device memory is entirely reserved up front by a pooling
+ * allocator (so cudaMalloc fails or fragments the pool), and host applications or plugin hosts
+ * that forbid run-time allocation.  The paper has no counterpart; this call only removes the
+ * plan's allocations.
+ *
+ * It computes exactly what fdas_plan_create + fdas_templates_build + fdas_convolve_power compute
+ * for the same arguments (same validation, same kernels), but keeps the template bank, the FP64
+ * taps, the twiddle table and the status word in one file-scope device array of
+ * FDAS_STATIC_SCRATCH_BYTES bytes instead of plan memory.  That array exists on every GPU that
+ * loads the library and is held until the process exits.  The call makes no cudaMalloc, cudaFree
+ * or other allocating call.
+ *
+ *   n_bins, zmax, zstep, seg_len, tmpl_len   as for fdas_plan_create; in addition
+ *       Z*L*8 + Z*(m+1)*16 + L*8 (each rounded up to 256) + 256 bytes must fit in
+ *       FDAS_STATIC_SCRATCH_BYTES (the 2^22-bin, 201-template, L=2048, m=512 survey geometry
+ *       needs 4.96 MB), else FDAS_ERR_INVALID before any device work.
+ *   d_spectrum, d_plane, stream               as for fdas_convolve_power (caller-owned, 16-byte
+ *       aligned device memory; the plane is fully overwritten).
+ *
+ * Asynchronous on `stream`.  The first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.  The template bank is
+ * rebuilt (FP64, tens of ms for the survey geometry) whenever (zmax, zstep, seg_len, tmpl_len)
+ * differs from the previous call on the same device, and reused otherwise; the status word is
+ * cleared on every call.  All calls share the one array, which keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, other host threads without ordering) race.  A
+ * bounded device wait that gives up leaves the plane unspecified and is recorded only in the
+ * array's status word, which this call does not read back.  Returns FDAS_OK, FDAS_ERR_INVALID,
+ * FDAS_ERR_ALIGN, FDAS_ERR_NO_DEVICE, FDAS_ERR_UNSUPPORTED or FDAS_ERR_CUDA.
+ */
+#define FDAS_STATIC_SCRATCH_BYTES (8u << 20)
+int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len,
+                               const float* d_spectrum, float* d_plane, fdas_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

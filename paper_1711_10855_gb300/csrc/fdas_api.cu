@@ -421,3 +421,49 @@ int fdas_template_spectrum(fdas_plan* p, int z_idx, float* host_out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Helpers for the allocation-free entry point (fdas_static.cu): the same validation, template
+// build kernels and tensor-map encoding as the plan-based calls above, on caller-given memory.
+// ---------------------------------------------------------------------------------------
+namespace fdas {
+
+int validate_geometry(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len) {
+  return validate(n_bins, zmax, zstep, seg_len, tmpl_len);
+}
+
+cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist, int zmax, int zstep, int L,
+                                 int m, cudaStream_t st) {
+  static bool gl_ready = false;
+  static double gl_x[kGLPoints], gl_w[kGLPoints];
+  if (!gl_ready) {
+    gauss_legendre(kGLPoints, gl_x, gl_w);
+    gl_ready = true;
+  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(gl_x), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(gl_w), 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const int Z = 2 * (zmax / zstep) + 1, h = m / 2, n1 = conv_group_threads(L);
+  taps_kernel<<<Z, 256, 0, st>>>(taps, zmax, zstep, h);
+  const size_t tab = sizeof(double2) * (size_t)L;
+  e = cudaFuncSetAttribute(spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+  if (e != cudaSuccess) return e;
+  spectra_kernel<<<dim3((L + 255) / 256, Z), 256, tab, st>>>(taps, templates, L, h, n1);
+  twist_kernel<<<(L + 255) / 256, 256, 0, st>>>(twist, L, n1);
+  return cudaGetLastError();
+}
+
+int encode_spectrum_map(CUtensorMap* map, const void* d_spectrum, int64_t n_bins, int L) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return FDAS_ERR_CUDA;
+  cuuint64_t gdim[1] = {(cuuint64_t)n_bins};
+  cuuint64_t gstride[1] = {0};
+  cuuint32_t box[1] = {(cuuint32_t)(L < 256 ? L : 256)};
+  cuuint32_t estride[1] = {1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 1, const_cast<void*>(d_spectrum), gdim, gstride, box,
+                   estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+}  // namespace fdas

@@ -42,3 +42,11 @@ cudaError_t launch_segment_spectra(int L, const CUtensorMap* spec_map, const Seg
                                    int sm_count, cudaStream_t stream);
 
 }  // namespace fdas
+
+namespace fdas {
+// Used by the allocation-free entry point (defined in fdas_api.cu).
+int validate_geometry(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len);
+cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist, int zmax, int zstep, int L,
+                                 int m, cudaStream_t st);
+int encode_spectrum_map(CUtensorMap* map, const void* d_spectrum, int64_t n_bins, int L);
+}  // namespace fdas

@@ -1,0 +1,112 @@
+// fdas_static.cu -- fdas_convolve_power_static: the fused correlation without any device
+// allocation (declared in include/fdas.h).  The template bank, FP64 taps, twiddle table and
+// status word live in one file-scope device array instead of plan memory.
+#include <cstdint>
+#include <mutex>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fdas.h"
+#include "fdas_internal.h"
+
+namespace {
+
+// The scratch array.  In host code `g_static_scratch` is only a host-side stand-in for the
+// symbol: its device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_static_scratch[FDAS_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceScratch {
+  bool ready = false;
+  unsigned char* base = nullptr;   // device address of g_static_scratch on this device
+  int sm_count = 0;
+  bool have_bank = false;          // geometry of the template bank currently in the array
+  int zmax = -1, zstep = -1, L = -1, m = -1;
+};
+
+DeviceScratch g_dev[kMaxDevices];
+std::mutex g_mutex;
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len,
+                                          const float* d_spectrum, float* d_plane, fdas_stream_t stream) {
+  int rc = fdas::validate_geometry(n_bins, zmax, zstep, seg_len, tmpl_len);
+  if (rc != FDAS_OK) return rc;
+  const int L = seg_len, m = tmpl_len, h = m / 2, V = L - m;
+  const int Z = 2 * (zmax / zstep) + 1;
+  // layout inside the array: template spectra | taps | twiddles | status word
+  const size_t off_tmpl = 0;
+  const size_t off_taps = off_tmpl + round256(sizeof(float2) * (size_t)Z * L);
+  const size_t off_twist = off_taps + round256(sizeof(double2) * (size_t)Z * (m + 1));
+  const size_t off_status = off_twist + round256(sizeof(float2) * (size_t)L);
+  const size_t need = off_status + 256;
+  if (need > (size_t)FDAS_STATIC_SCRATCH_BYTES) return FDAS_ERR_INVALID;
+  if (!d_spectrum || !d_plane) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u))
+    return FDAS_ERR_ALIGN;
+
+  int ndev = 0, dev = 0, major = 0, minor = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return FDAS_ERR_NO_DEVICE;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDAS_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  if (major != 10 || minor != 3) return FDAS_ERR_UNSUPPORTED;
+
+  std::lock_guard<std::mutex> lock(g_mutex);
+  DeviceScratch& s = g_dev[dev];
+  if (!s.ready) {
+    // once per device, with that device current: the array's device address
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr) {
+      cudaGetLastError();
+      return FDAS_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FDAS_ERR_CUDA;
+    s.base = static_cast<unsigned char*>(ptr);
+    s.sm_count = sms;
+    s.ready = true;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float2* templates = reinterpret_cast<float2*>(s.base + off_tmpl);
+  double2* taps = reinterpret_cast<double2*>(s.base + off_taps);
+  float2* twist = reinterpret_cast<float2*>(s.base + off_twist);
+  int* status = reinterpret_cast<int*>(s.base + off_status);
+
+  if (!s.have_bank || s.zmax != zmax || s.zstep != zstep || s.L != L || s.m != m) {
+    s.have_bank = false;
+    if (fdas::build_templates_into(taps, templates, twist, zmax, zstep, L, m, st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+    s.have_bank = true;
+    s.zmax = zmax;
+    s.zstep = zstep;
+    s.L = L;
+    s.m = m;
+  }
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return FDAS_ERR_CUDA;
+
+  CUtensorMap map;
+  rc = fdas::encode_spectrum_map(&map, d_spectrum, n_bins, L);
+  if (rc != FDAS_OK) return rc;
+  fdas::ConvParams q;
+  q.templates = templates;
+  q.twist = twist;
+  q.plane = d_plane;
+  q.status = status;
+  q.n_bins = n_bins;
+  q.nseg = (n_bins + V - 1) / V;
+  q.units = 0;
+  q.Z = Z;
+  q.V = V;
+  q.h = h;
+  return fdas::launch_convolve(L, &map, q, s.sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}

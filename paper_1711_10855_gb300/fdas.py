@@ -23,7 +23,8 @@ ERRORS = {
 }
 EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_templates_build",
             "fdas_convolve_power", "fdas_check", "fdas_destroy", "fdas_plan_dims",
-            "fdas_template_taps", "fdas_template_spectrum", "fdas_segment_spectra"]
+            "fdas_template_taps", "fdas_template_spectrum", "fdas_segment_spectra",
+            "fdas_convolve_power_static"]
 
 _lock = threading.Lock()
 _lib = None
@@ -66,6 +67,8 @@ def lib() -> ctypes.CDLL:
             L.fdas_template_spectrum.restype = i32
             L.fdas_segment_spectra.argtypes = [vp, vp, vp, vp]
             L.fdas_segment_spectra.restype = i32
+            L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
+            L.fdas_convolve_power_static.restype = i32
             _lib = L
     return _lib
 
@@ -159,6 +162,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def convolve_power_static(n_bins: int, zmax: int, zstep: int, seg_len: int, tmpl_len: int,
+                          spectrum, plane, stream=None):
+    """fdas_convolve_power_static: the same plane as Plan(...).convolve_power, without any device
+    allocation (template bank in the library's fixed-size static device array)."""
+    _check(lib().fdas_convolve_power_static(int(n_bins), int(zmax), int(zstep), int(seg_len), int(tmpl_len),
+                                            _ptr(spectrum), _ptr(plane), _stream(stream)),
+           "fdas_convolve_power_static")
 
 
 def plane_shape(plan: Plan) -> tuple[int, int]:
