@@ -109,9 +109,12 @@ __global__ void taps_kernel(double2* taps, int zmax, int zstep, int h) {
   }
 }
 
-__device__ __forceinline__ int layout_of(int k, int n1) {
+// Float offset of the real part of element k in the pair-major structure-of-arrays layout
+// (lane k1 = k % n1, k2 = k / n1; pair p = k2/2 of lane k1 is the float4 at p*n1 + k1 holding
+// re(2p), re(2p+1), im(2p), im(2p+1)); the imaginary part is 2 floats further.
+__host__ __device__ __forceinline__ int pair_layout_re(int k, int n1) {
   const int k1 = k % n1, k2 = k / n1;
-  return ((k2 >> 1) * n1 + k1) * 2 + (k2 & 1);
+  return ((k2 >> 1) * n1 + k1) * 4 + (k2 & 1);
 }
 
 // a1, part 2: T_z[k] = (1/L) sum_{j=0}^{m} conj(Hn_{j-h}) exp(+i 2pi k j / L) in FP64 (the
@@ -138,17 +141,25 @@ __global__ void spectra_kernel(const double2* taps, float2* templates, int L, in
     re += hq.x * e.x + hq.y * e.y;   // Re(conj(h) e)
     im += hq.x * e.y - hq.y * e.x;   // Im(conj(h) e)
   }
-  templates[(size_t)zi * L + layout_of(k, n1)] = make_float2((float)(re / L), (float)(im / L));
+  float* dst = reinterpret_cast<float*>(templates + (size_t)zi * L);
+  const int off = pair_layout_re(k, n1);
+  dst[off] = (float)(re / L);
+  dst[off + 2] = (float)(im / L);
 }
 
-// Inter-pass twiddles exp(+i 2pi n2 k1 / L), n2 < L/n1, k1 < n1, in the kernel layout.
+// Inter-pass twiddles exp(+i 2pi n2 k1 / L), n2 < N2 = L/n1, k1 < n1: lane k1's pair j holds
+// n2 = j and n2 = j + N2/2 (float4 at j*n1 + k1: re, re, im, im).
 __global__ void twist_kernel(float2* tw, int L, int n1) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= L) return;
   const int k1 = idx % n1, n2 = idx / n1;
+  const int h2 = L / n1 / 2;
   double sn, cs;
   sincospi(2.0 * (double)(((long long)n2 * k1) % L) / (double)L, &sn, &cs);
-  tw[((n2 >> 1) * n1 + k1) * 2 + (n2 & 1)] = make_float2((float)cs, (float)sn);
+  float* dst = reinterpret_cast<float*>(tw);
+  const int off = ((n2 % h2) * n1 + k1) * 4 + n2 / h2;
+  dst[off] = (float)cs;
+  dst[off + 2] = (float)sn;
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -410,11 +421,11 @@ int fdas_template_spectrum(fdas_plan* p, int z_idx, float* host_out) {
     std::free(tmp);
     return FDAS_ERR_CUDA;
   }
+  const float* f = reinterpret_cast<const float*>(tmp);
   for (int k = 0; k < p->L; ++k) {
-    const int k1 = k % p->n1, k2 = k / p->n1;
-    const float2 v = tmp[((k2 >> 1) * p->n1 + k1) * 2 + (k2 & 1)];
-    host_out[2 * k] = v.x;
-    host_out[2 * k + 1] = v.y;
+    const int off = pair_layout_re(k, p->n1);
+    host_out[2 * k] = f[off];
+    host_out[2 * k + 1] = f[off + 2];
   }
   std::free(tmp);
   return FDAS_OK;

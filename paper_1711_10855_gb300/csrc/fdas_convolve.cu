@@ -35,77 +35,91 @@ namespace fdas {
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int L_, int N1_, int P_>
+template <int L_, int N1_, int P_, int XR_>
 struct ConvCfg {
   static constexpr int L = L_;
-  static constexpr int N1 = N1_;
-  static constexpr int N2 = L / N1;
+  static constexpr int N1 = N1_;           // lanes per transform
+  static constexpr int N2 = L / N1;        // points per lane in pass 1
+  static constexpr int H2 = N2 / 2;        // pass-1 pairs per lane
   static constexpr int F = 32 / N1;        // transform groups per warp
   static constexpr int W = 8;              // compute warps per CTA
   static constexpr int P = P_;             // warps sharing one segment
   static constexpr int G = F * W / P;      // segments resident per CTA
   static constexpr int R = 4;              // template ring slots
-  static constexpr int C = N2 / N1;        // exchange rounds
+  static constexpr int C = N2 / N1;        // pass-2 columns per lane
+  static constexpr int CP = C / 2;         // pass-2 column pairs per lane (= exchange row rounds)
+  static constexpr int XR = XR_;           // exchange sub-rounds (lane halves writing in turn)
+  static constexpr int XCOLS = N1 / XR;    // exchange tile columns per sub-round
+  static constexpr int XPITCH = XCOLS + 1; // 16-byte entries per tile row (odd: conflict-free)
+  static constexpr int XGROUP = N1 * XPITCH;
+  static constexpr int XWARP = F * XGROUP;
   static constexpr int LOG_N1 = ilog2(N1);
   static constexpr int LOG_N2 = ilog2(N2);
-  static constexpr int TR_PITCH = N1 + 1;  // float2 per exchange-tile row (bank-conflict padding)
-  static constexpr int TR_GROUP = N1 * TR_PITCH;
-  static constexpr int TR_WARP = F * TR_GROUP;
   static constexpr int BOX = L < 256 ? L : 256;   // TMA box (elements of 8 bytes)
   static constexpr size_t OFF_X = 0;
   static constexpr size_t OFF_T = OFF_X + (size_t)G * L * 8;
   static constexpr size_t OFF_TW = OFF_T + (size_t)R * L * 8;
-  static constexpr size_t OFF_TR = OFF_TW + (size_t)L * 8;
-  static constexpr size_t OFF_BAR = align_up(OFF_TR + (size_t)W * TR_WARP * 8, 128);
+  static constexpr size_t OFF_XB = OFF_TW + (size_t)L * 8;
+  static constexpr size_t OFF_BAR = align_up(OFF_XB + (size_t)W * XWARP * 16, 128);
   static constexpr size_t SMEM = OFF_BAR + 256;
-  static_assert(N1 * N2 == L && N2 % N1 == 0 && 32 % N1 == 0, "bad decomposition");
+  static_assert(N1 * N2 == L && C >= 2 && C % 2 == 0 && 32 % N1 == 0, "bad decomposition");
+  static_assert(N1 % XR == 0 && XCOLS % 2 == 0, "bad exchange split");
   static_assert(L % BOX == 0, "segment must be whole boxes");
   static_assert(SMEM <= 232448, "shared memory budget");
 };
 
 // ---------------------------------------------------------------------------------------
 // Shared per-lane pieces of the transform
+//
+// Buffer layout of a segment spectrum, a template spectrum and the twiddle table (L complex
+// values each), "pair-major structure of arrays": lane k1 of the first pass owns the pairs
+// p = 0..H2-1; pair p of lane k1 is the float4 at index p*N1 + k1 holding
+// (re(e0), re(e1), im(e0), im(e1)).  For spectra and templates e0, e1 are the elements
+// k = k1 + N1*(2p) and k1 + N1*(2p+1); for the twiddle table they are exp(+i 2pi n2 k1 / L)
+// for n2 = p and p + H2.  One 128-bit load gives a packed pair ready for f32x2 arithmetic.
 // ---------------------------------------------------------------------------------------
 
-// Element k = k1 + N1*k2 of a segment spectrum / template / twiddle table lives at this
-// float2 index of its L-entry buffer (pairs k2 = 2p, 2p+1 of one lane are adjacent: float4).
-template <class Cfg>
-__device__ __forceinline__ int layout_index(int k1, int k2) {
-  return ((k2 >> 1) * Cfg::N1 + k1) * 2 + (k2 & 1);
-}
-
-// v[n2] *= tw[n2][k1] (CONJ: by its conjugate), n2 = 1..N2-1.
+// Pass 1 of the inverse transform on entry: v[i] = (Y[k1 + N1*bitrev(i)], Y[k1 + N1*(bitrev(i)+1)]),
+// i < H2 (bitrev over log2 N2 bits of an even index is < H2).  After fft_split_pairs:
+// v[j] = (Z[j], Z[j + H2]) for the lane's N2-point DFT; the twist then multiplies by the
+// twiddle pair of row j.
 template <class Cfg, bool CONJ>
-__device__ __forceinline__ void apply_twist(float2 (&v)[Cfg::N2], const float2* __restrict__ stw, int k1) {
-  static_for<Cfg::N2 / 2>([&](auto pp) {
-    constexpr int p = decltype(pp)::value;
-    const float4 w = reinterpret_cast<const float4*>(stw)[p * Cfg::N1 + k1];
-    if constexpr (p > 0) {
-      v[2 * p] = CONJ ? cmul_conj_b(v[2 * p], make_float2(w.x, w.y)) : cmul(v[2 * p], make_float2(w.x, w.y));
-    }
-    v[2 * p + 1] =
-        CONJ ? cmul_conj_b(v[2 * p + 1], make_float2(w.z, w.w)) : cmul(v[2 * p + 1], make_float2(w.z, w.w));
+__device__ __forceinline__ void apply_twist2(cp2 (&v)[Cfg::H2], const float4* __restrict__ stw, int k1) {
+  static_for<Cfg::H2>([&](auto jj) {
+    constexpr int j = decltype(jj)::value;
+    const cp2 w = cp2_from(stw[j * Cfg::N1 + k1]);
+    v[j] = CONJ ? cmul2_conj(v[j], w) : cmul2(v[j], w);
   });
 }
 
-// Pass 1 result v[n2] (lane k1) -> exchange -> pass 2 per column; calls out(r, n1, value)
-// with the transform's output at n = r*N1 + k1 + N2*n1 held by this lane.
+// Exchange + pass 2.  Lane k1's pair j = r*N1 + t holds columns n2 = t + N1*r and
+// t + N1*(r + CP) of row k1; lane t gathers, for its column pair r, the entries of all N1 lanes
+// and runs two N1-point DFTs in lockstep.  Round r moves rows j in [r*N1, (r+1)*N1) through a
+// tile of N1 rows x XCOLS lanes (XR sub-rounds, lanes [h*XCOLS, (h+1)*XCOLS) writing in turn).
+// out(r, n1, pair) receives (y[t + N1*r + N2*n1], y[t + N1*(r+CP) + N2*n1]).
 template <class Cfg, int SIGN, class Out>
-__device__ __forceinline__ void exchange_and_pass2(float2 (&v)[Cfg::N2], float2* tr, int k1, Out&& out) {
-  static_for<Cfg::C>([&](auto rr) {
+__device__ __forceinline__ void exchange_and_pass2(cp2 (&v)[Cfg::H2], float4* xb, int k1, Out&& out) {
+  static_for<Cfg::CP>([&](auto rr) {
     constexpr int r = decltype(rr)::value;
-    __syncwarp();
-    static_for<Cfg::N1>([&](auto ii) {
-      constexpr int i = decltype(ii)::value;
-      tr[i * Cfg::TR_PITCH + k1] = v[r * Cfg::N1 + i];
+    cp2 u[Cfg::N1];
+    static_for<Cfg::XR>([&](auto hh) {
+      constexpr int h = decltype(hh)::value;
+      __syncwarp();
+      if (k1 / Cfg::XCOLS == h) {
+        const int c = k1 - h * Cfg::XCOLS;
+        static_for<Cfg::N1>([&](auto ii) {
+          constexpr int i = decltype(ii)::value;
+          xb[i * Cfg::XPITCH + c] = cp2_to(v[r * Cfg::N1 + i]);
+        });
+      }
+      __syncwarp();
+      static_for<Cfg::XCOLS>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        constexpr int src = h * Cfg::XCOLS + c;   // the writing lane k1'
+        u[bitrev(src, Cfg::LOG_N1)] = cp2_from(xb[k1 * Cfg::XPITCH + c]);
+      });
     });
-    __syncwarp();
-    float2 u[Cfg::N1];
-    static_for<Cfg::N1>([&](auto jj) {
-      constexpr int j = decltype(jj)::value;
-      u[j] = tr[k1 * Cfg::TR_PITCH + bitrev(j, Cfg::LOG_N1)];
-    });
-    fft_dit<Cfg::N1, SIGN>(u);
+    fft_pair_columns<Cfg::N1, SIGN>(u);
     static_for<Cfg::N1>([&](auto nn) {
       constexpr int n1 = decltype(nn)::value;
       out(std::integral_constant<int, r>{}, std::integral_constant<int, n1>{}, u[n1]);
@@ -113,19 +127,30 @@ __device__ __forceinline__ void exchange_and_pass2(float2 (&v)[Cfg::N2], float2*
   });
 }
 
-// Forward FFT (Eq. 3) of one segment held in natural order in sx; calls
-// out(r, n1, X[r*N1 + k1 + N2*n1]).
+// Forward FFT (Eq. 3) of one segment held in natural order (complex64) in sx;
+// out(r, n1, pair) receives (X[t + N1*r + N2*n1], X[t + N1*(r+CP) + N2*n1]).
 template <class Cfg, class Out>
-__device__ __forceinline__ void forward_transform(const float2* sx, const float2* __restrict__ stw, float2* tr,
+__device__ __forceinline__ void forward_transform(const float2* sx, const float4* __restrict__ stw, float4* xb,
                                                   int k1, Out&& out) {
-  float2 v[Cfg::N2];
-  static_for<Cfg::N2>([&](auto kk) {
-    constexpr int k2 = decltype(kk)::value;
-    v[bitrev(k2, Cfg::LOG_N2)] = sx[k1 + Cfg::N1 * k2];
+  cp2 v[Cfg::H2];
+  static_for<Cfg::H2>([&](auto ii) {
+    constexpr int i = decltype(ii)::value;
+    constexpr int k2 = bitrev(i, Cfg::LOG_N2);
+    const float2 a = sx[k1 + Cfg::N1 * k2];
+    const float2 b = sx[k1 + Cfg::N1 * (k2 + 1)];
+    v[i] = cp2{make_float2(a.x, b.x), make_float2(a.y, b.y)};
   });
-  fft_dit<Cfg::N2, -1>(v);
-  apply_twist<Cfg, true>(v, stw, k1);
-  exchange_and_pass2<Cfg, -1>(v, tr, k1, out);
+  fft_split_pairs<Cfg::N2, -1>(v);
+  apply_twist2<Cfg, true>(v, stw, k1);
+  exchange_and_pass2<Cfg, -1>(v, xb, k1, out);
+}
+
+// Store X[n] (held by lane t = n mod N1) into the pair-major layout of the inverse transform.
+template <class Cfg>
+__device__ __forceinline__ void store_spectrum_element(float* sx, int t, int k2, float re, float im) {
+  const int base = ((k2 >> 1) * Cfg::N1 + t) * 4 + (k2 & 1);
+  sx[base] = re;
+  sx[base + 2] = im;
 }
 
 // Device status word: set bit 0 when a bounded wait gave up.
@@ -145,7 +170,7 @@ __global__ void __launch_bounds__(256, 1)
   float2* sX = reinterpret_cast<float2*>(smem + Cfg::OFF_X);
   float2* sT = reinterpret_cast<float2*>(smem + Cfg::OFF_T);
   float2* sTw = reinterpret_cast<float2*>(smem + Cfg::OFF_TW);
-  float2* sTr = reinterpret_cast<float2*>(smem + Cfg::OFF_TR);
+  float4* sXb = reinterpret_cast<float4*>(smem + Cfg::OFF_XB);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR);
   uint64_t* segbar = full + R;
   uint64_t* twbar = segbar + 1;
@@ -158,7 +183,8 @@ __global__ void __launch_bounds__(256, 1)
   const int par = warp % P;
   const int seg_slot = (warp / P) * Cfg::F + gw;
   float2* myX = sX + seg_slot * L;
-  float2* myTr = sTr + warp * Cfg::TR_WARP + gw * Cfg::TR_GROUP;
+  float4* myXb = sXb + warp * Cfg::XWARP + gw * Cfg::XGROUP;
+  const float4* stw4 = reinterpret_cast<const float4*>(sTw);
 
   const int64_t U = p.units;
   const int64_t u0 = (int64_t)blockIdx.x * U / gridDim.x;
@@ -222,10 +248,12 @@ __global__ void __launch_bounds__(256, 1)
     seg_in_flight = false;
     seg_phase ^= 1u;
     if (par == 0) {
-      // a3: forward FFT in place; X[n] goes to the slot of the inverse transform's first pass
-      forward_transform<Cfg>(myX, sTw, myTr, k1, [&](auto rr, auto nn, float2 val) {
-        constexpr int k2p = decltype(rr)::value + Cfg::C * decltype(nn)::value;
-        myX[layout_index<Cfg>(k1, k2p)] = val;
+      // a3: forward FFT in place; X[n] goes to the pair-major layout of the inverse transform
+      forward_transform<Cfg>(myX, stw4, myXb, k1, [&](auto rr, auto nn, const cp2& x) {
+        constexpr int r = decltype(rr)::value, n1 = decltype(nn)::value;
+        float* sx = reinterpret_cast<float*>(myX);
+        store_spectrum_element<Cfg>(sx, k1, r + Cfg::C * n1, x.re.x, x.im.x);
+        store_spectrum_element<Cfg>(sx, k1, r + Cfg::CP + Cfg::C * n1, x.re.y, x.im.y);
       });
     }
     __syncthreads();
@@ -247,14 +275,13 @@ __global__ void __launch_bounds__(256, 1)
       const int64_t z = (u0 + i) % p.Z;
       const float2* st = sT + (size_t)slot * L;
 
-      // a4: Y = X * T in the first pass's register order (bit-reversed for the DIT)
-      float2 v[Cfg::N2];
-      static_for<Cfg::N2 / 2>([&](auto pp) {
+      // a4: Y = X * T, loaded as packed pairs in the first pass's bit-reversed order
+      cp2 v[Cfg::H2];
+      static_for<Cfg::H2>([&](auto pp) {
         constexpr int q = decltype(pp)::value;
-        const float4 x = reinterpret_cast<const float4*>(myX)[q * N1 + k1];
-        const float4 t = reinterpret_cast<const float4*>(st)[q * N1 + k1];
-        v[bitrev(2 * q, Cfg::LOG_N2)] = cmul(make_float2(x.x, x.y), make_float2(t.x, t.y));
-        v[bitrev(2 * q + 1, Cfg::LOG_N2)] = cmul(make_float2(x.z, x.w), make_float2(t.z, t.w));
+        const cp2 x = cp2_from(reinterpret_cast<const float4*>(myX)[q * N1 + k1]);
+        const cp2 t = cp2_from(reinterpret_cast<const float4*>(st)[q * N1 + k1]);
+        v[bitrev(2 * q, Cfg::LOG_N2)] = cmul2(x, t);
       });
       // release the template slot; the last of the W/P consumers refills it R positions ahead
       __syncwarp();
@@ -270,13 +297,17 @@ __global__ void __launch_bounds__(256, 1)
         }
       }
       // a5: inverse FFT
-      fft_dit<Cfg::N2, +1>(v);
-      apply_twist<Cfg, false>(v, sTw, k1);
+      fft_split_pairs<Cfg::N2, +1>(v);
+      apply_twist2<Cfg, false>(v, stw4, k1);
       float* row = p.plane + z * p.n_bins + segbase;
-      exchange_and_pass2<Cfg, +1>(v, myTr, k1, [&](auto rr, auto nn, float2 y) {
+      exchange_and_pass2<Cfg, +1>(v, myXb, k1, [&](auto rr, auto nn, const cp2& y) {
         // a6 + a7: keep n < V (and inside the spectrum), store |y|^2
-        const int n = decltype(rr)::value * N1 + k1 + Cfg::N2 * decltype(nn)::value;
-        if (n < lim) __stcs(row + n, power(y));
+        constexpr int r = decltype(rr)::value, n1 = decltype(nn)::value;
+        const float2 pw = power2(y);
+        const int n_lo = r * N1 + k1 + Cfg::N2 * n1;
+        const int n_hi = n_lo + Cfg::CP * N1;
+        if (n_lo < lim) __stcs(row + n_lo, pw.x);
+        if (n_hi < lim) __stcs(row + n_hi, pw.y);
       });
     }
   }
@@ -299,8 +330,8 @@ __global__ void __launch_bounds__(256, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   float2* sX = reinterpret_cast<float2*>(smem);
   float2* sTw = sX + (size_t)GS * L;
-  float2* sTr = sTw + L;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + align_up(((size_t)GS * L + L + 8 * Cfg::TR_WARP) * 8, 128));
+  float4* sXb = reinterpret_cast<float4*>(sTw + L);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + align_up(((size_t)GS * L + L) * 8 + (size_t)8 * Cfg::XWARP * 16, 128));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gw = lane / N1, k1 = lane % N1;
   const int slot = warp * Cfg::F + gw;
@@ -330,17 +361,20 @@ __global__ void __launch_bounds__(256, 1)
   const int64_t s = s0 + slot;
   float2* dst = p.out + s * L;
   const bool valid = s < p.nseg;
-  forward_transform<Cfg>(sX + (size_t)slot * L, sTw, sTr + warp * Cfg::TR_WARP + gw * Cfg::TR_GROUP, k1,
-                         [&](auto rr, auto nn, float2 val) {
+  forward_transform<Cfg>(sX + (size_t)slot * L, reinterpret_cast<const float4*>(sTw),
+                         sXb + warp * Cfg::XWARP + gw * Cfg::XGROUP, k1, [&](auto rr, auto nn, const cp2& x) {
                            const int n = decltype(rr)::value * N1 + k1 + Cfg::N2 * decltype(nn)::value;
-                           if (valid) dst[n] = val;
+                           if (valid) {
+                             dst[n] = make_float2(x.re.x, x.im.x);
+                             dst[n + Cfg::CP * N1] = make_float2(x.re.y, x.im.y);
+                           }
                          });
 }
 
 // ---------------------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------------------
-int conv_group_threads(int L) { return L <= 512 ? 16 : 32; }
+int conv_group_threads(int L) { return L <= 256 ? 8 : (L <= 1024 ? 16 : 32); }
 
 template <class Cfg>
 static cudaError_t launch_conv_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
@@ -358,7 +392,7 @@ static cudaError_t launch_conv_cfg(const CUtensorMap* map, const ConvParams& p, 
 template <class Cfg>
 static cudaError_t launch_seg_cfg(const CUtensorMap* map, const SegParams& p, cudaStream_t st) {
   constexpr int GS = 8 * Cfg::F;
-  constexpr size_t smem = align_up(((size_t)GS * Cfg::L + Cfg::L + 8 * Cfg::TR_WARP) * 8, 128) + 64;
+  constexpr size_t smem = align_up(((size_t)GS * Cfg::L + Cfg::L) * 8 + (size_t)8 * Cfg::XWARP * 16, 128) + 64;
   auto kern = fdas_segment_spectra_kernel<Cfg>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -367,10 +401,10 @@ static cudaError_t launch_seg_cfg(const CUtensorMap* map, const SegParams& p, cu
   return cudaGetLastError();
 }
 
-using Cfg256 = ConvCfg<256, 16, 1>;
-using Cfg512 = ConvCfg<512, 16, 1>;
-using Cfg1024 = ConvCfg<1024, 32, 1>;
-using Cfg2048 = ConvCfg<2048, 32, 2>;
+using Cfg256 = ConvCfg<256, 8, 1, 1>;
+using Cfg512 = ConvCfg<512, 16, 1, 1>;
+using Cfg1024 = ConvCfg<1024, 16, 2, 1>;
+using Cfg2048 = ConvCfg<2048, 32, 2, 2>;
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
   switch (L) {

@@ -169,6 +169,116 @@ __device__ __forceinline__ void fft_dit(float2 (&v)[N]) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Packed pairs: two complex numbers as structure-of-arrays in two 64-bit register pairs,
+// processed by the sm_100+ packed FP32 instructions (add/mul/fma .f32x2): one instruction does
+// the same operation on both members, which halves the issue slots of the transform.
+// ---------------------------------------------------------------------------------------
+struct cp2 {
+  float2 re;   // (a.re, b.re)
+  float2 im;   // (a.im, b.im)
+};
+
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Element-wise complex products of two pairs (4 packed instructions).
+__device__ __forceinline__ cp2 cmul2(const cp2& a, const cp2& b) {
+  return cp2{fma2(a.re, b.re, mul2(make_float2(-a.im.x, -a.im.y), b.im)), fma2(a.re, b.im, mul2(a.im, b.re))};
+}
+__device__ __forceinline__ cp2 cmul2_conj(const cp2& a, const cp2& b) {   // a * conj(b)
+  return cp2{fma2(a.re, b.re, mul2(a.im, b.im)), fma2(a.im, b.re, mul2(make_float2(-a.re.x, -a.re.y), b.im))};
+}
+__device__ __forceinline__ float2 power2(const cp2& a) { return fma2(a.re, a.re, mul2(a.im, a.im)); }
+__device__ __forceinline__ cp2 cp2_from(float4 v) { return cp2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 cp2_to(const cp2& v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+
+// Packed DIT butterfly on two pairs: a' = a + w b, b' = a - w b, w = exp(SIGN i 2pi J/M), the
+// same twiddle for both members.  Same FMA forms as the scalar butterfly.
+template <int J, int M, int SIGN>
+__device__ __forceinline__ void butterfly2(cp2& a, cp2& b) {
+  constexpr CosSin cs = cossin_2pi(J, M);
+  constexpr double wc = cs.c;
+  constexpr double ws = SIGN * cs.s;
+  if constexpr (J == 0) {
+    const cp2 t = a;
+    a = cp2{add2(t.re, b.re), add2(t.im, b.im)};
+    b = cp2{sub2(t.re, b.re), sub2(t.im, b.im)};
+  } else if constexpr (4 * J == M) {
+    const cp2 t = a;
+    if constexpr (SIGN > 0) {   // w b = (-b.im, b.re)
+      a = cp2{sub2(t.re, b.im), add2(t.im, b.re)};
+      b = cp2{add2(t.re, b.im), sub2(t.im, b.re)};
+    } else {                    // w b = (b.im, -b.re)
+      a = cp2{add2(t.re, b.im), sub2(t.im, b.re)};
+      b = cp2{sub2(t.re, b.im), add2(t.im, b.re)};
+    }
+  } else if constexpr (cabsd(wc) >= cabsd(ws)) {
+    constexpr float t = (float)(ws / wc);
+    constexpr float c = (float)wc;
+    const float2 ur = fma2(bc(-t), b.im, b.re);
+    const float2 ui = fma2(bc(t), b.re, b.im);
+    const cp2 s = a;
+    a = cp2{fma2(bc(c), ur, s.re), fma2(bc(c), ui, s.im)};
+    b = cp2{fma2(bc(-c), ur, s.re), fma2(bc(-c), ui, s.im)};
+  } else {
+    constexpr float ct = (float)(wc / ws);
+    constexpr float sn = (float)ws;
+    const float2 ur = fma2(bc(ct), b.re, make_float2(-b.im.x, -b.im.y));
+    const float2 ui = fma2(bc(ct), b.im, b.re);
+    const cp2 s = a;
+    a = cp2{fma2(bc(sn), ur, s.re), fma2(bc(sn), ui, s.im)};
+    b = cp2{fma2(bc(-sn), ur, s.re), fma2(bc(-sn), ui, s.im)};
+  }
+}
+
+template <int N, int SIGN, int S, int I>
+__device__ __forceinline__ void stage_butterfly2(cp2 (&v)[N]) {
+  constexpr int span = 1 << S;
+  constexpr int blk = (I / span) * (2 * span);
+  constexpr int j = I % span;
+  butterfly2<j, 2 * span, SIGN>(v[blk + j], v[blk + j + span]);
+}
+template <int N, int SIGN, int S, int... I>
+__device__ __forceinline__ void fft_stage2(cp2 (&v)[N], std::integer_sequence<int, I...>) {
+  (stage_butterfly2<N, SIGN, S, I>(v), ...);
+}
+template <int N, int SIGN, int... S>
+__device__ __forceinline__ void fft_stages2(cp2 (&v)[N], std::integer_sequence<int, S...>) {
+  (fft_stage2<N, SIGN, S>(v, std::make_integer_sequence<int, N / 2>{}), ...);
+}
+
+// Two independent N-point DFTs in lockstep ("columns" a and b of each pair):
+// on entry v[i] = (a[bitrev(i)], b[bitrev(i)]), on exit v[m] = (A[m], B[m]).
+template <int N, int SIGN>
+__device__ __forceinline__ void fft_pair_columns(cp2 (&v)[N]) {
+  fft_stages2<N, SIGN>(v, std::make_integer_sequence<int, ilog2(N)>{});
+}
+
+template <int N, int SIGN, int J>
+__device__ __forceinline__ void last_stage_scalar(cp2 (&v)[N / 2]) {
+  float2 a = make_float2(v[J].re.x, v[J].im.x);
+  float2 b = make_float2(v[J].re.y, v[J].im.y);
+  butterfly<J, N, SIGN>(a, b);
+  v[J] = cp2{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+}
+template <int N, int SIGN, int... J>
+__device__ __forceinline__ void last_stage_all(cp2 (&v)[N / 2], std::integer_sequence<int, J...>) {
+  (last_stage_scalar<N, SIGN, J>(v), ...);
+}
+
+// One N-point DFT held as N/2 pairs v[i] = (x[bitrev(i)], x[bitrev(i + N/2)]): the first
+// log2(N)-1 stages are two N/2-point DFTs in lockstep (packed), the last stage pairs the two
+// members of each pair (scalar FMA butterflies).  On exit v[j] = (X[j], X[j + N/2]).
+template <int N, int SIGN>
+__device__ __forceinline__ void fft_split_pairs(cp2 (&v)[N / 2]) {
+  fft_stages2<N / 2, SIGN>(v, std::make_integer_sequence<int, ilog2(N) - 1>{});
+  last_stage_all<N, SIGN>(v, std::make_integer_sequence<int, N / 2>{});
+}
+
+// ---------------------------------------------------------------------------------------
 // mbarrier and bulk asynchronous copies (TMA), with time-bounded waits
 // ---------------------------------------------------------------------------------------
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
