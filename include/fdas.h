@@ -118,6 +118,16 @@ int fdas_convolve_power(fdas_plan* plan, const float* d_spectrum, float* d_plane
  */
 int fdas_check(fdas_plan* plan, fdas_stream_t stream);
 
+/*
+ * Failure-detection self test (no counterpart in the paper): launches one thread that waits, for
+ * at most limit_ns nanoseconds (1 us .. 2 s), on a device barrier that nothing ever completes,
+ * through the same bounded wait the fused kernel uses, and records the timeout in the plan's
+ * status word.  The next fdas_check() on the stream returns FDAS_ERR_TIMEOUT and clears it; the
+ * context stays usable.  Asynchronous on `stream`; FDAS_ERR_INVALID for a NULL plan or a limit
+ * out of range.
+ */
+int fdas_selftest_wait_timeout(fdas_plan* plan, int64_t limit_ns, fdas_stream_t stream);
+
 /* Free the plan's device memory (synchronises the device first).  NULL is a no-op. */
 int fdas_destroy(fdas_plan* plan);
 

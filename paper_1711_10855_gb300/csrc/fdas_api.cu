@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "fdas.h"
+#include "fdas_device.cuh"
 #include "fdas_internal.h"
 
 struct fdas_plan {
@@ -160,6 +161,16 @@ __global__ void twist_kernel(float2* tw, int L, int n1) {
   const int off = ((n2 % h2) * n1 + k1) * 4 + n2 / h2;
   dst[off] = (float)cs;
   dst[off + 2] = (float)sn;
+}
+
+// Failure-detection self test: one thread waits, with the given bound, on an mbarrier whose
+// phase nothing completes, and records the timeout in the status word exactly as the fused
+// kernel does.  The wait ends by itself; the context stays usable.
+__global__ void wait_selftest_kernel(int* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  fdas::mbar_init(&bar, 1);
+  fdas::fence_barrier_init();
+  if (!fdas::mbar_wait(&bar, 0, limit_ns)) atomicOr(status, 1);
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -381,6 +392,13 @@ int fdas_check(fdas_plan* p, fdas_stream_t stream) {
     return FDAS_ERR_TIMEOUT;
   }
   return FDAS_OK;
+}
+
+int fdas_selftest_wait_timeout(fdas_plan* p, int64_t limit_ns, fdas_stream_t stream) {
+  if (!p || limit_ns < 1000 || limit_ns > 2000000000LL) return FDAS_ERR_INVALID;
+  wait_selftest_kernel<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p->d_status,
+                                                                             (unsigned long long)limit_ns);
+  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 int fdas_destroy(fdas_plan* p) {

@@ -14,13 +14,16 @@
 //   a7  |y|^2 stored with streaming (evict-first) stores into plane[z][s*V + n].
 //
 // Transform of length L = N1 * N2 by a group of N1 lanes, N2 points per lane (four-step):
-//   pass 1: each lane k1 holds Y[k1 + N1*k2], k2 < N2, and does an N2-point DFT in registers,
-//   twist:  multiply by exp(SIGN i 2pi n2 k1 / L),
-//   exchange through a padded shared-memory tile (C = N2/N1 rounds of N1 x N1),
-//   pass 2: lane t holds column n2 = r*N1 + t and does an N1-point DFT in registers; output
-//           index n = n2 + N2*n1, so lane t ends with every n = t (mod N1).
-// The paper's design (Section 2: shuffle stage for N <= 32, shared memory above) is replaced
-// by two register passes and a single shared-memory exchange per transform.
+//   pass 1: lane k1 holds Y[k1 + N1*k2], k2 < N2, as N2/2 packed pairs and does its N2-point DFT
+//           in registers (two N2/2-point DFTs in lockstep with packed f32x2 butterflies, then one
+//           scalar stage joining them),
+//   twist:  multiply by exp(SIGN i 2pi n2 k1 / L) (packed),
+//   exchange: one shared-memory transposition of 16-byte pair entries through a padded tile,
+//   pass 2: lane t holds two columns n2 (a packed pair) and runs two N1-point DFTs in lockstep;
+//           output index n = n2 + N2*n1, so lane t ends with outputs n = t (mod N1).
+// The paper's design (Section 2: shuffle stage for N <= 32, shared memory above, 4 elements per
+// thread) is replaced by two register passes with compile-time FMA butterflies on packed pairs
+// and a single shared-memory exchange per transform.
 //
 // Work decomposition: a CTA of 8 warps owns G consecutive segments at a time ("group"); the
 // flattened (group, z) list is split into contiguous equal ranges, one per CTA (grid = #SMs),
@@ -35,7 +38,7 @@ namespace fdas {
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int L_, int N1_, int P_, int XR_>
+template <int L_, int N1_, int P_, int XR_, int R_ = 4>
 struct ConvCfg {
   static constexpr int L = L_;
   static constexpr int N1 = N1_;           // lanes per transform
@@ -45,7 +48,7 @@ struct ConvCfg {
   static constexpr int W = 8;              // compute warps per CTA
   static constexpr int P = P_;             // warps sharing one segment
   static constexpr int G = F * W / P;      // segments resident per CTA
-  static constexpr int R = 4;              // template ring slots
+  static constexpr int R = R_;             // template ring slots
   static constexpr int C = N2 / N1;        // pass-2 columns per lane
   static constexpr int CP = C / 2;         // pass-2 column pairs per lane (= exchange row rounds)
   static constexpr int XR = XR_;           // exchange sub-rounds (lane halves writing in turn)
@@ -129,9 +132,9 @@ __device__ __forceinline__ void exchange_and_pass2(cp2 (&v)[Cfg::H2], float4* xb
 
 // Forward FFT (Eq. 3) of one segment held in natural order (complex64) in sx;
 // out(r, n1, pair) receives (X[t + N1*r + N2*n1], X[t + N1*(r+CP) + N2*n1]).
-template <class Cfg, class Out>
-__device__ __forceinline__ void forward_transform(const float2* sx, const float4* __restrict__ stw, float4* xb,
-                                                  int k1, Out&& out) {
+template <class Cfg, class Twist, class Out>
+__device__ __forceinline__ void forward_transform_with(const float2* sx, Twist&& twist_conj, float4* xb, int k1,
+                                                       Out&& out) {
   cp2 v[Cfg::H2];
   static_for<Cfg::H2>([&](auto ii) {
     constexpr int i = decltype(ii)::value;
@@ -141,8 +144,33 @@ __device__ __forceinline__ void forward_transform(const float2* sx, const float4
     v[i] = cp2{make_float2(a.x, b.x), make_float2(a.y, b.y)};
   });
   fft_split_pairs<Cfg::N2, -1>(v);
-  apply_twist2<Cfg, true>(v, stw, k1);
+  twist_conj(v);
   exchange_and_pass2<Cfg, -1>(v, xb, k1, out);
+}
+template <class Cfg, class Out>
+__device__ __forceinline__ void forward_transform(const float2* sx, const float4* __restrict__ stw, float4* xb,
+                                                  int k1, Out&& out) {
+  forward_transform_with<Cfg>(sx, [&](cp2 (&v)[Cfg::H2]) { apply_twist2<Cfg, true>(v, stw, k1); }, xb, k1, out);
+}
+
+// Twist with the twiddle pairs held in this lane's TMEM row (4 columns per pair, chunks of 4 pairs).
+template <class Cfg, bool CONJ>
+__device__ __forceinline__ void apply_twist_tmem(cp2 (&v)[Cfg::H2], uint32_t tw_addr) {
+  static_assert(Cfg::H2 % 8 == 0, "twist chunking");
+  static_for<Cfg::H2 / 8>([&](auto cc) {
+    constexpr int c = decltype(cc)::value;
+    float r0[16], r1[16];
+    tmem_ld16(tw_addr + 32 * c, r0);
+    tmem_ld16(tw_addr + 32 * c + 16, r1);
+    tmem_wait_ld();
+    static_for<4>([&](auto qq) {
+      constexpr int q = decltype(qq)::value;
+      const cp2 w0 = cp2{make_float2(r0[4 * q], r0[4 * q + 1]), make_float2(r0[4 * q + 2], r0[4 * q + 3])};
+      const cp2 w1 = cp2{make_float2(r1[4 * q], r1[4 * q + 1]), make_float2(r1[4 * q + 2], r1[4 * q + 3])};
+      v[8 * c + q] = CONJ ? cmul2_conj(v[8 * c + q], w0) : cmul2(v[8 * c + q], w0);
+      v[8 * c + 4 + q] = CONJ ? cmul2_conj(v[8 * c + 4 + q], w1) : cmul2(v[8 * c + 4 + q], w1);
+    });
+  });
 }
 
 // Store X[n] (held by lane t = n mod N1) into the pair-major layout of the inverse transform.
@@ -321,6 +349,251 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Variant with the segment spectra and the twiddle table in tensor memory (one column pair per
+// lane: N2 = 2*N1, i.e. L = 512 and 2048).  Every warp owns its own segment(s); the template of
+// each position is read from the shared-memory ring by all 8 warps.  Per inverse transform the
+// shared-memory traffic is the template (L*8 bytes) and the exchange (2*L*8 bytes); the
+// spectrum and the twiddles come from TMEM, a separate store, which relieves the shared-memory
+// bandwidth that otherwise co-limits the kernel with the FP32 pipe.
+// ---------------------------------------------------------------------------------------
+template <int L_, int N1_>
+struct TmemCfg {
+  static constexpr int L = L_;
+  static constexpr int N1 = N1_;
+  static constexpr int N2 = L / N1;
+  static constexpr int H2 = N2 / 2;
+  static constexpr int F = 32 / N1;
+  static constexpr int W = 8;
+  static constexpr int P = 1;
+  static constexpr int G = F * W;          // segments resident per CTA: one group of lanes each
+  static constexpr int R = 4;
+  static constexpr int C = 2;
+  static constexpr int CP = 1;
+  static constexpr int XR = 1;
+  static constexpr int XCOLS = N1;
+  static constexpr int XPITCH = N1 + 1;
+  static constexpr int XGROUP = N1 * XPITCH;
+  static constexpr int XWARP = F * XGROUP;
+  static constexpr int LOG_N1 = ilog2(N1);
+  static constexpr int LOG_N2 = ilog2(N2);
+  static constexpr int BOX = L < 256 ? L : 256;
+  // per-warp shared region: staging of its segments, then its exchange tiles
+  static constexpr size_t REGION = align_up(((size_t)F * L * 8 > (size_t)XWARP * 16) ? (size_t)F * L * 8
+                                                                                     : (size_t)XWARP * 16, 128);
+  static constexpr size_t OFF_T = 0;
+  static constexpr size_t OFF_REG = OFF_T + (size_t)R * L * 8;
+  static constexpr size_t OFF_BAR = align_up(OFF_REG + (size_t)W * REGION, 128);
+  static constexpr size_t SMEM = OFF_BAR + 256;
+  // TMEM columns of each quadrant: twiddles, then the spectra of its two warps
+  static constexpr uint32_t TMEM_COLS = 512;
+  static constexpr uint32_t COL_TW = 0;
+  static constexpr uint32_t COL_X = 2 * N2;
+  static_assert(N2 == 2 * N1 && 32 % N1 == 0, "one column pair per lane");
+  static_assert(6 * N2 <= (int)TMEM_COLS, "TMEM columns");
+  static_assert(SMEM <= 232448, "shared memory budget");
+};
+
+template <class Cfg>
+__global__ void __launch_bounds__(256, 1)
+    fdas_convolve_tmem_kernel(const __grid_constant__ CUtensorMap spec_map, const ConvParams p) {
+  constexpr int L = Cfg::L, N1 = Cfg::N1, R = Cfg::R, G = Cfg::G, H2 = Cfg::H2, W = Cfg::W;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float2* sT = reinterpret_cast<float2*>(smem + Cfg::OFF_T);
+  unsigned char* sReg = smem + Cfg::OFF_REG;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR);
+  uint64_t* segbar = full + R;
+  int64_t* issued_pos = reinterpret_cast<int64_t*>(segbar + 1);
+  unsigned* cnt = reinterpret_cast<unsigned*>(issued_pos + R);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(cnt + R);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cnt + R + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gw = lane / N1, k1 = lane % N1;
+  float2* myRegion = reinterpret_cast<float2*>(sReg + (size_t)warp * Cfg::REGION);
+  float2* mySeg = myRegion + (size_t)gw * L;
+  float4* myXb = reinterpret_cast<float4*>(myRegion) + gw * Cfg::XGROUP;
+
+  const int64_t U = p.units;
+  const int64_t u0 = (int64_t)blockIdx.x * U / gridDim.x;
+  const int64_t u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
+  const int64_t npos = u1 - u0;
+  if (npos <= 0) return;
+
+  if (tid == 0) {
+    for (int r = 0; r < R; ++r) {
+      mbar_init(&full[r], 1);
+      cnt[r] = 0u;
+      issued_pos[r] = -1;
+    }
+    mbar_init(segbar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem_row = *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t tw_addr = tmem_row + Cfg::COL_TW;
+  const uint32_t x_addr = tmem_row + Cfg::COL_X + (uint32_t)(warp >> 2) * (2 * Cfg::N2);
+
+  auto issue_template = [&](int64_t i) {
+    const int slot = (int)(i % R);
+    const int64_t z = (u0 + i) % p.Z;
+    issued_pos[slot] = i;
+    mbar_arrive_expect_tx(&full[slot], L * 8);
+    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)z * L, L * 8, &full[slot]);
+  };
+  if (tid == 0) {
+    const int64_t first = npos < R ? npos : R;
+    for (int64_t i = 0; i < first; ++i) issue_template(i);
+  }
+  // twiddle pairs of lane k1 into this quadrant's TMEM rows (one warp per quadrant)
+  if (warp < 4) {
+    const float4* tw4 = reinterpret_cast<const float4*>(p.twist);
+    static_for<H2 / 4>([&](auto cc) {
+      constexpr int c = decltype(cc)::value;
+      float r[16];
+      static_for<4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+        const float4 w = __ldg(tw4 + (4 * c + q) * N1 + k1);
+        r[4 * q] = w.x;
+        r[4 * q + 1] = w.y;
+        r[4 * q + 2] = w.z;
+        r[4 * q + 3] = w.w;
+      });
+      tmem_st16(tw_addr + 16 * c, r);
+    });
+    tmem_wait_st();
+  }
+  tmem_fence_before_sync();
+  int alive = 1;
+  uint32_t seg_phase = 0;
+  bool seg_in_flight = false;
+  const int64_t g_first = u0 / p.Z, g_last = (u1 - 1) / p.Z;
+  for (int64_t grp = g_first; grp <= g_last; ++grp) {
+    const int64_t a = (grp * p.Z > u0 ? grp * p.Z : u0) - u0;
+    const int64_t b = ((grp + 1) * p.Z < u1 ? (grp + 1) * p.Z : u1) - u0;
+    // every warp is done with its region (previous exchanges) before segments land in it
+    alive = __syncthreads_and(alive && !*abort_flag);
+    tmem_fence_after_sync();
+    if (!alive) break;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(segbar, G * L * 8);
+      for (int j = 0; j < G; ++j) {
+        float2* dst = reinterpret_cast<float2*>(sReg + (size_t)(j / Cfg::F) * Cfg::REGION) + (size_t)(j % Cfg::F) * L;
+        const int64_t x0 = (grp * G + j) * (int64_t)p.V - p.h;
+        for (int bx = 0; bx < L / Cfg::BOX; ++bx)
+          tma_load_1d(dst + bx * Cfg::BOX, &spec_map, (int32_t)(x0 + bx * Cfg::BOX), segbar);
+      }
+    }
+    seg_in_flight = true;
+    alive = __syncthreads_and(mbar_wait(segbar, seg_phase) ? 1 : 0);
+    if (!alive) {
+      if (tid == 0) report_timeout(p.status, abort_flag);
+      break;
+    }
+    seg_in_flight = false;
+    seg_phase ^= 1u;
+
+    // a3: forward FFT of this lane group's segment; X pairs (k2 = 2p, 2p+1) go to TMEM
+    {
+      float xr[16];
+      forward_transform_with<Cfg>(
+          mySeg, [&](cp2 (&v)[H2]) { apply_twist_tmem<Cfg, true>(v, tw_addr); }, myXb, k1,
+          [&](auto, auto nn, const cp2& x) {
+            constexpr int n1 = decltype(nn)::value;   // pair p = n1
+            xr[4 * (n1 & 3)] = x.re.x;
+            xr[4 * (n1 & 3) + 1] = x.re.y;
+            xr[4 * (n1 & 3) + 2] = x.im.x;
+            xr[4 * (n1 & 3) + 3] = x.im.y;
+            if constexpr ((n1 & 3) == 3) tmem_st16(x_addr + 4 * (n1 - 3), xr);
+          });
+      tmem_wait_st();
+    }
+
+    const int64_t s = grp * G + warp * Cfg::F + gw;
+    const int64_t segbase = s * (int64_t)p.V;
+    const int64_t lim64 = p.n_bins - segbase < (int64_t)p.V ? p.n_bins - segbase : (int64_t)p.V;
+    const int lim = lim64 > 0 ? (int)lim64 : 0;
+    for (int64_t i = a; i < b; ++i) {
+      const int slot = (int)(i % R);
+      int ok = *abort_flag ? 0 : (mbar_wait(&full[slot], (uint32_t)((i / R) & 1)) ? 1 : 0);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) report_timeout(p.status, abort_flag);
+        break;
+      }
+      const int64_t z = (u0 + i) % p.Z;
+      const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
+
+      // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
+      cp2 v[H2];
+      static_for<H2 / 8>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        float x0[16], x1[16];
+        tmem_ld16(x_addr + 32 * c, x0);
+        tmem_ld16(x_addr + 32 * c + 16, x1);
+        float4 t[8];
+        static_for<8>([&](auto qq) {
+          constexpr int q = decltype(qq)::value;
+          t[q] = st4[(8 * c + q) * N1 + k1];
+        });
+        tmem_wait_ld();
+        static_for<8>([&](auto qq) {
+          constexpr int q = decltype(qq)::value;
+          constexpr int pp = 8 * c + q;
+          const float* xs = q < 4 ? &x0[4 * q] : &x1[4 * (q - 4)];
+          const cp2 x = cp2{make_float2(xs[0], xs[1]), make_float2(xs[2], xs[3])};
+          v[bitrev(2 * pp, Cfg::LOG_N2)] = cmul2(x, cp2_from(t[q]));
+        });
+      });
+      // release the template slot; the last of the W consumers refills it R positions ahead
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        const unsigned old = atomicAdd(&cnt[slot], 1u);
+        if ((old + 1u) % (unsigned)W == 0u) {
+          __threadfence_block();
+          if (i + R < npos) {
+            fence_proxy_async_smem();
+            issue_template(i + R);
+          }
+        }
+      }
+      // a5: inverse FFT
+      fft_split_pairs<Cfg::N2, +1>(v);
+      apply_twist_tmem<Cfg, false>(v, tw_addr);
+      float* row = p.plane + z * p.n_bins + segbase;
+      exchange_and_pass2<Cfg, +1>(v, myXb, k1, [&](auto, auto nn, const cp2& y) {
+        // a6 + a7: keep n < V (and inside the spectrum), store |y|^2
+        constexpr int n1 = decltype(nn)::value;
+        const float2 pw = power2(y);
+        const int n_lo = k1 + Cfg::N2 * n1;
+        const int n_hi = n_lo + N1;
+        if (n_lo < lim) __stcs(row + n_lo, pw.x);
+        if (n_hi < lim) __stcs(row + n_hi, pw.y);
+      });
+    }
+    tmem_fence_before_sync();
+  }
+
+  // After a timeout, wait (bounded) for this CTA's copies still in flight; always free TMEM.
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (tid == 0 && (*abort_flag || !alive)) {
+    for (int r = 0; r < R; ++r)
+      if (issued_pos[r] >= 0) (void)mbar_wait(&full[r], (uint32_t)((issued_pos[r] / R) & 1));
+    if (seg_in_flight) (void)mbar_wait(segbar, seg_phase);
+  }
+  if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
+}
+
 // Forward transforms only (steps a2 + a3), natural-order output, for tests of the FFT.
 template <class Cfg>
 __global__ void __launch_bounds__(256, 1)
@@ -393,6 +666,7 @@ template <class Cfg>
 static cudaError_t launch_seg_cfg(const CUtensorMap* map, const SegParams& p, cudaStream_t st) {
   constexpr int GS = 8 * Cfg::F;
   constexpr size_t smem = align_up(((size_t)GS * Cfg::L + Cfg::L) * 8 + (size_t)8 * Cfg::XWARP * 16, 128) + 64;
+  static_assert(smem <= 232448, "shared memory budget of the segment-spectra kernel");
   auto kern = fdas_segment_spectra_kernel<Cfg>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -404,14 +678,27 @@ static cudaError_t launch_seg_cfg(const CUtensorMap* map, const SegParams& p, cu
 using Cfg256 = ConvCfg<256, 8, 1, 1>;
 using Cfg512 = ConvCfg<512, 16, 1, 1>;
 using Cfg1024 = ConvCfg<1024, 16, 2, 1>;
-using Cfg2048 = ConvCfg<2048, 32, 2, 2>;
+using Cfg2048 = ConvCfg<2048, 32, 4, 1, 2>;
+
+template <class Cfg>
+static cudaError_t launch_tmem_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
+  auto kern = fdas_convolve_tmem_kernel<Cfg>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  ConvParams q = p;
+  const int64_t ngroups = (p.nseg + Cfg::G - 1) / Cfg::G;
+  q.units = ngroups * p.Z;
+  const int64_t grid = q.units < sm_count ? q.units : sm_count;
+  kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(*map, q);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
   switch (L) {
     case 256: return launch_conv_cfg<Cfg256>(map, p, sm_count, st);
-    case 512: return launch_conv_cfg<Cfg512>(map, p, sm_count, st);
+    case 512: return launch_tmem_cfg<TmemCfg<512, 16>>(map, p, sm_count, st);
     case 1024: return launch_conv_cfg<Cfg1024>(map, p, sm_count, st);
-    case 2048: return launch_conv_cfg<Cfg2048>(map, p, sm_count, st);
+    case 2048: return launch_tmem_cfg<TmemCfg<2048, 32>>(map, p, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -421,7 +708,7 @@ cudaError_t launch_segment_spectra(int L, const CUtensorMap* map, const SegParam
     case 256: return launch_seg_cfg<Cfg256>(map, p, st);
     case 512: return launch_seg_cfg<Cfg512>(map, p, st);
     case 1024: return launch_seg_cfg<Cfg1024>(map, p, st);
-    case 2048: return launch_seg_cfg<Cfg2048>(map, p, st);
+    case 2048: return launch_seg_cfg<ConvCfg<2048, 32, 2, 2>>(map, p, st);   // two-round exchange fits
     default: return cudaErrorInvalidValue;
   }
 }

@@ -24,7 +24,7 @@ ERRORS = {
 EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_templates_build",
             "fdas_convolve_power", "fdas_check", "fdas_destroy", "fdas_plan_dims",
             "fdas_template_taps", "fdas_template_spectrum", "fdas_segment_spectra",
-            "fdas_convolve_power_static"]
+            "fdas_convolve_power_static", "fdas_selftest_wait_timeout"]
 
 _lock = threading.Lock()
 _lib = None
@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             L.fdas_template_spectrum.restype = i32
             L.fdas_segment_spectra.argtypes = [vp, vp, vp, vp]
             L.fdas_segment_spectra.restype = i32
+            L.fdas_selftest_wait_timeout.argtypes = [vp, i64, vp]
+            L.fdas_selftest_wait_timeout.restype = i32
             L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
             L.fdas_convolve_power_static.restype = i32
             _lib = L
@@ -132,6 +134,10 @@ class Plan:
     def segment_spectra(self, spectrum, out, stream=None):
         _check(lib().fdas_segment_spectra(self._h, _ptr(spectrum), _ptr(out), _stream(stream)),
                "fdas_segment_spectra")
+
+    def selftest_wait_timeout(self, limit_ns: int, stream=None):
+        _check(lib().fdas_selftest_wait_timeout(self._h, int(limit_ns), _stream(stream)),
+               "fdas_selftest_wait_timeout")
 
     def check(self, stream=None):
         _check(lib().fdas_check(self._h, _stream(stream)), "fdas_check")

@@ -77,6 +77,7 @@ def test_null_plan_calls(lib):
     assert lib.fdas_template_taps(None, 0, None) == -1
     assert lib.fdas_template_spectrum(None, 0, None) == -1
     assert lib.fdas_segment_spectra(None, None, None, None) == -1
+    assert lib.fdas_selftest_wait_timeout(None, ctypes.c_int64(1000000), None) == -1
 
 
 def test_no_device_is_an_error_not_a_fallback(lib, cuda_available):

@@ -265,3 +265,24 @@ def test_survey_recovers_injected_chirps(survey_plane):
         zi, dr = np.unravel_index(np.argmax(win), win.shape)
         assert abs(zs[zi] - c.z) <= w.zstep + 1e-9, (c, zs[zi])
         assert abs(lo + dr - c.r_mean) <= 1.0, (c, lo + dr)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(dev):
+    """A device wait on a barrier that nothing completes gives up after its bound (50 ms),
+    fdas_check reports FDAS_ERR_TIMEOUT once, and the next correlation still runs correctly."""
+    import time
+    fdas = _fdas()
+    n = 4096
+    spec = synth.noise_spectrum(n, seed=3)
+    with fdas.Plan(n, 4, 2, 512, 64) as plan:
+        plan.build_templates()
+        plan.check()
+        t0 = time.perf_counter()
+        plan.selftest_wait_timeout(50_000_000)
+        with pytest.raises(fdas.FdasError) as e:
+            plan.check()
+        assert e.value.code == -8
+        assert time.perf_counter() - t0 < 5.0
+        plan.check()   # cleared
+    got = gpu_plane(spec, 4, 2, 512, 64, dev)
+    assert_rows_close(got, oracle.plane_rows(spec, 4, 2, 64))
