@@ -394,7 +394,9 @@ struct TmemCfg {
   static_assert(SMEM <= 232448, "shared memory budget");
 };
 
-template <class Cfg>
+// NV: pass-2 output rows n1 < NV can hold valid outputs (NV >= ceil(V / N2)); rows n1 >= NV are
+// dropped at compile time, which also removes the butterfly halves that only feed them.
+template <class Cfg, int NV>
 __global__ void __launch_bounds__(256, 1)
     fdas_convolve_tmem_kernel(const __grid_constant__ CUtensorMap spec_map, const ConvParams p) {
   constexpr int L = Cfg::L, N1 = Cfg::N1, R = Cfg::R, G = Cfg::G, H2 = Cfg::H2, W = Cfg::W;
@@ -572,11 +574,13 @@ __global__ void __launch_bounds__(256, 1)
       exchange_and_pass2<Cfg, +1>(v, myXb, k1, [&](auto, auto nn, const cp2& y) {
         // a6 + a7: keep n < V (and inside the spectrum), store |y|^2
         constexpr int n1 = decltype(nn)::value;
-        const float2 pw = power2(y);
-        const int n_lo = k1 + Cfg::N2 * n1;
-        const int n_hi = n_lo + N1;
-        if (n_lo < lim) __stcs(row + n_lo, pw.x);
-        if (n_hi < lim) __stcs(row + n_hi, pw.y);
+        if constexpr (n1 < NV) {
+          const float2 pw = power2(y);
+          const int n_lo = k1 + Cfg::N2 * n1;
+          const int n_hi = n_lo + N1;
+          if (n_lo < lim) __stcs(row + n_lo, pw.x);
+          if (n_hi < lim) __stcs(row + n_hi, pw.y);
+        }
       });
     }
     tmem_fence_before_sync();
@@ -680,9 +684,9 @@ using Cfg512 = ConvCfg<512, 16, 1, 1>;
 using Cfg1024 = ConvCfg<1024, 16, 2, 1>;
 using Cfg2048 = ConvCfg<2048, 32, 4, 1, 2>;
 
-template <class Cfg>
-static cudaError_t launch_tmem_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
-  auto kern = fdas_convolve_tmem_kernel<Cfg>;
+template <class Cfg, int NV>
+static cudaError_t launch_tmem_nv(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
+  auto kern = fdas_convolve_tmem_kernel<Cfg, NV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
   ConvParams q = p;
@@ -691,6 +695,15 @@ static cudaError_t launch_tmem_cfg(const CUtensorMap* map, const ConvParams& p, 
   const int64_t grid = q.units < sm_count ? q.units : sm_count;
   kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(*map, q);
   return cudaGetLastError();
+}
+
+// Smallest instantiated NV >= ceil(V / N2): N1*3/4, N1*7/8 or N1.
+template <class Cfg>
+static cudaError_t launch_tmem_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
+  const int rows = (p.V + Cfg::N2 - 1) / Cfg::N2;
+  if (rows <= Cfg::N1 * 3 / 4) return launch_tmem_nv<Cfg, Cfg::N1 * 3 / 4>(map, p, sm_count, st);
+  if (rows <= Cfg::N1 * 7 / 8) return launch_tmem_nv<Cfg, Cfg::N1 * 7 / 8>(map, p, sm_count, st);
+  return launch_tmem_nv<Cfg, Cfg::N1>(map, p, sm_count, st);
 }
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
