@@ -136,6 +136,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (the replicas' timed durations); identity at N=1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells_per_rank: int, steps: int, world: int, t_max_s: float) -> float:
+    """Whole-job cells/s of N independent replicas: all ranks' cells over the slowest rank's time."""
+    return cells_per_rank * steps * world / t_max_s
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -259,16 +275,9 @@ def run_ours(args):
     plan.check(stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
-    t_local = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = max_over_ranks(sum(step_ms) / 1e3, dev)
     cells = plan.n_z * w.n_bins
-    value = cells * args.steps * world / t_max
+    value = replica_throughput(cells, args.steps, world, t_max)
 
     # ---- end to end through the public call with host buffers -----------------------------
     h_spec = torch.from_numpy(spec.view(np.float32).copy()).pin_memory()
@@ -290,13 +299,8 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plan.check(stream)
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = cells * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+    e2e_value = replica_throughput(cells, e2e_steps, world, e2e_s)
 
     if rank != 0:
         if world > 1:
