@@ -156,6 +156,52 @@ int fdas_template_spectrum(fdas_plan* plan, int z_idx, float* host_out);
 int fdas_segment_spectra(fdas_plan* plan, const float* d_spectrum, float* d_out,
                          fdas_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batches: many spectra of uneven lengths (e.g. the de-dispersion trials of one observation,
+ * Section 1) correlated by ONE persistent kernel launch.  Every spectrum i has its own n_bins[i]
+ * and zmax[i]; zstep, seg_len and tmpl_len are shared.  The batch holds one template bank for the
+ * largest zmax (rows for smaller zmax are its middle rows).  The flattened (spectrum, segment
+ * group, template) work is split into equal contiguous ranges over the SMs.  Only segment
+ * lengths with a descriptor-driven kernel are accepted (512 and 2048).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fdas_batch fdas_batch;
+
+/* Host call: validate every (n_bins[i], zmax[i], zstep, seg_len, tmpl_len) as fdas_plan_create
+ * does, allocate the bank, the descriptor table (device) and its pinned staging.  NULL on
+ * failure, code in fdas_batch_last_error().  count in [1, 2^20]; arrays are host memory. */
+fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax, int zstep, int seg_len,
+                              int tmpl_len);
+int fdas_batch_last_error(void);
+
+/* Template bank (as fdas_templates_build) for zmax = max_i zmax[i]; stream-ordered. */
+int fdas_batch_templates_build(fdas_batch* batch, fdas_stream_t stream);
+
+/* Correlate every spectrum: d_spectra[i] (n_bins[i] complex64) -> d_planes[i] (Z_i x n_bins[i]
+ * float32, Z_i = 2*zmax[i]/zstep + 1, row z_idx = (z + zmax[i])/zstep); both host arrays of
+ * 16-byte-aligned device pointers.  Synchronises `stream` once (the descriptor staging is
+ * reused), copies the descriptor table, then issues ONE kernel launch -- directly, or with
+ * use_graph != 0 as a CUDA graph holding that launch (captured and instantiated on first use,
+ * replayed afterwards).  FDAS_ERR_NOT_BUILT / INVALID / ALIGN / CUDA as fdas_convolve_power. */
+int fdas_batch_convolve_power(fdas_batch* batch, const float* const* d_spectra, float* const* d_planes,
+                              int use_graph, fdas_stream_t stream);
+
+/* As fdas_check for the batch's status word. */
+int fdas_batch_check(fdas_batch* batch, fdas_stream_t stream);
+int fdas_batch_destroy(fdas_batch* batch);
+/* seg_len, template-bank rows, total work units, segments resident per CTA; NULL outputs skipped. */
+int fdas_batch_info(const fdas_batch* batch, int* seg_len, int* z_bank, int64_t* units, int* segments_per_cta);
+
+/*
+ * Autotuner (no counterpart in the paper): for each candidate segment length, build a batch,
+ * time three launches on the caller's buffers with CUDA events (after one warm-up) and keep the
+ * fastest; candidates that cannot serve the batch (tmpl_len > L/2, no kernel) are skipped and
+ * reported as -1 in ms_out (n_candidates floats, may be NULL).  The planes are overwritten.
+ * Returns FDAS_OK with *best_seg_len set, FDAS_ERR_INVALID if no candidate applies.
+ */
+int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int zstep, int tmpl_len,
+                        const int* seg_len_candidates, int n_candidates, const float* const* d_spectra,
+                        float* const* d_planes, fdas_stream_t stream, int* best_seg_len, float* ms_out);
+
 /*
  * Allocation-free variant of fdas_convolve_power, for callers that cannot allocate device
  * memory: code on a latency-critical path where cudaMalloc may synchronise the device and take

@@ -348,6 +348,7 @@ int fdas_convolve_power(fdas_plan* p, const float* d_spectrum, float* d_plane, f
   int rc = make_spectrum_map(p, d_spectrum);
   if (rc != FDAS_OK) return rc;
   fdas::ConvParams q;
+  q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
   q.templates = p->d_templates;
   q.twist = p->d_twist;
   q.plane = d_plane;

@@ -1,0 +1,286 @@
+// fdas_batch.cu -- many spectra of uneven lengths in one persistent launch (declared in
+// include/fdas.h): the batch object, its CUDA-graph launch and the segment-length autotuner.
+//
+// A batch holds one template bank for the largest |z| of its spectra (a spectrum with a smaller
+// zmax uses the middle rows of the same bank: the templates depend on z only) and a device table
+// of per-spectrum descriptors.  One launch of the descriptor-driven kernel correlates every
+// spectrum with its templates; the flattened (spectrum, segment group, template) work is split
+// into equal contiguous ranges over the SMs, so uneven lengths do not unbalance the grid.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fdas.h"
+#include "fdas_internal.h"
+
+struct fdas_batch {
+  int device = 0, sm_count = 0;
+  int count = 0;
+  int L = 0, m = 0, h = 0, V = 0, zstep = 1, zmax_bank = 0, Z_bank = 0, G = 0;
+  std::vector<int64_t> n_bins;
+  std::vector<int> zmax;
+  int64_t units = 0;
+  float2* d_templates = nullptr;
+  double2* d_taps = nullptr;
+  float2* d_twist = nullptr;
+  int* d_status = nullptr;
+  fdas::SpecDesc* d_descs = nullptr;
+  fdas::SpecDesc* h_descs = nullptr;   // pinned staging of the descriptor table
+  bool built = false;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+thread_local int g_batch_error = FDAS_OK;
+
+void free_batch(fdas_batch* b) {
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  cudaFree(b->d_templates);
+  cudaFree(b->d_taps);
+  cudaFree(b->d_twist);
+  cudaFree(b->d_status);
+  cudaFree(b->d_descs);
+  if (b->h_descs) cudaFreeHost(b->h_descs);
+  delete b;
+}
+
+fdas::BatchParams batch_params(const fdas_batch* b) {
+  fdas::BatchParams q;
+  std::memset(&q, 0, sizeof(q));
+  q.templates = b->d_templates;
+  q.twist = b->d_twist;
+  q.status = b->d_status;
+  q.descs = b->d_descs;
+  q.count = b->count;
+  q.units = b->units;
+  q.V = b->V;
+  q.h = b->h;
+  return q;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdas_batch_last_error(void) { return g_batch_error; }
+
+fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax, int zstep, int seg_len,
+                              int tmpl_len) {
+  g_batch_error = FDAS_OK;
+  if (count < 1 || count > (1 << 20) || !n_bins || !zmax || zstep < 1) {
+    g_batch_error = FDAS_ERR_INVALID;
+    return nullptr;
+  }
+  int zmax_bank = 0;
+  for (int i = 0; i < count; ++i) {
+    const int rc = fdas::validate_geometry(n_bins[i], zmax[i], zstep, seg_len, tmpl_len);
+    if (rc != FDAS_OK) {
+      g_batch_error = rc;
+      return nullptr;
+    }
+    if (zmax[i] > zmax_bank) zmax_bank = zmax[i];
+  }
+  const int G = fdas::batch_segments_per_cta(seg_len);
+  if (G == 0) {   // no descriptor-driven kernel for this segment length
+    g_batch_error = FDAS_ERR_INVALID;
+    return nullptr;
+  }
+  int ndev = 0, dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    g_batch_error = FDAS_ERR_NO_DEVICE;
+    return nullptr;
+  }
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    g_batch_error = FDAS_ERR_CUDA;
+    return nullptr;
+  }
+  if (major != 10 || minor != 3) {
+    g_batch_error = FDAS_ERR_UNSUPPORTED;
+    return nullptr;
+  }
+  fdas_batch* b = new (std::nothrow) fdas_batch();
+  if (!b) {
+    g_batch_error = FDAS_ERR_ALLOC;
+    return nullptr;
+  }
+  b->device = dev;
+  b->sm_count = sms;
+  b->count = count;
+  b->L = seg_len;
+  b->m = tmpl_len;
+  b->h = tmpl_len / 2;
+  b->V = seg_len - tmpl_len;
+  b->zstep = zstep;
+  b->zmax_bank = zmax_bank;
+  b->Z_bank = 2 * (zmax_bank / zstep) + 1;
+  b->G = G;
+  b->n_bins.assign(n_bins, n_bins + count);
+  b->zmax.assign(zmax, zmax + count);
+  const size_t ntap = (size_t)tmpl_len + 1;
+  if (cudaMalloc(&b->d_templates, sizeof(float2) * (size_t)b->Z_bank * b->L) != cudaSuccess ||
+      cudaMalloc(&b->d_taps, sizeof(double2) * (size_t)b->Z_bank * ntap) != cudaSuccess ||
+      cudaMalloc(&b->d_twist, sizeof(float2) * (size_t)b->L) != cudaSuccess ||
+      cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_descs, sizeof(fdas::SpecDesc) * (size_t)count) != cudaSuccess ||
+      cudaHostAlloc(&b->h_descs, sizeof(fdas::SpecDesc) * (size_t)count, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    g_batch_error = FDAS_ERR_ALLOC;
+    return nullptr;
+  }
+  if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    free_batch(b);
+    g_batch_error = FDAS_ERR_CUDA;
+    return nullptr;
+  }
+  // static part of the descriptor table: sizes, template rows and unit ranges
+  int64_t base = 0;
+  for (int i = 0; i < count; ++i) {
+    fdas::SpecDesc& d = b->h_descs[i];
+    std::memset(&d, 0, sizeof(d));
+    d.n_bins = n_bins[i];
+    d.nseg = (n_bins[i] + b->V - 1) / b->V;
+    d.ngroups = (d.nseg + G - 1) / G;
+    d.Z = 2 * (zmax[i] / zstep) + 1;
+    d.z_off = (zmax_bank - zmax[i]) / zstep;
+    d.unit_base = base;
+    base += d.ngroups * d.Z;
+  }
+  b->units = base;
+  return b;
+}
+
+int fdas_batch_templates_build(fdas_batch* b, fdas_stream_t stream) {
+  if (!b) return FDAS_ERR_INVALID;
+  if (fdas::build_templates_into(b->d_taps, b->d_templates, b->d_twist, b->zmax_bank, b->zstep, b->L, b->m,
+                                 reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  b->built = true;
+  return FDAS_OK;
+}
+
+int fdas_batch_convolve_power(fdas_batch* b, const float* const* d_spectra, float* const* d_planes, int use_graph,
+                              fdas_stream_t stream) {
+  if (!b || !d_spectra || !d_planes) return FDAS_ERR_INVALID;
+  if (!b->built) return FDAS_ERR_NOT_BUILT;
+  for (int i = 0; i < b->count; ++i) {
+    if (!d_spectra[i] || !d_planes[i]) return FDAS_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(d_spectra[i]) & 15u) || (reinterpret_cast<uintptr_t>(d_planes[i]) & 15u))
+      return FDAS_ERR_ALIGN;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the pinned staging may still feed a previous call's copy: wait for it on this stream's order
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FDAS_ERR_CUDA;
+  for (int i = 0; i < b->count; ++i) {
+    b->h_descs[i].spec = reinterpret_cast<const float2*>(d_spectra[i]);
+    b->h_descs[i].plane = d_planes[i];
+  }
+  if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(fdas::SpecDesc) * (size_t)b->count, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  const fdas::BatchParams q = batch_params(b);
+  if (!use_graph) return fdas::launch_batch(b->L, q, b->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  if (!b->graph_exec) {
+    // capture the persistent launch once; its parameters (table address, sizes) never change
+    if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+    const cudaError_t le = fdas::launch_batch(b->L, q, b->sm_count, b->capture_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return FDAS_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&b->graph_exec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      b->graph_exec = nullptr;
+      return FDAS_ERR_CUDA;
+    }
+    b->graph = g;
+  }
+  return cudaGraphLaunch(b->graph_exec, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_batch_check(fdas_batch* b, fdas_stream_t stream) {
+  if (!b) return FDAS_ERR_INVALID;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpy(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (status != 0) {
+    cudaMemset(b->d_status, 0, sizeof(int));
+    return FDAS_ERR_TIMEOUT;
+  }
+  return FDAS_OK;
+}
+
+int fdas_batch_destroy(fdas_batch* b) {
+  if (!b) return FDAS_OK;
+  cudaDeviceSynchronize();
+  free_batch(b);
+  return FDAS_OK;
+}
+
+int fdas_batch_info(const fdas_batch* b, int* seg_len, int* z_bank, int64_t* units, int* segments_per_cta) {
+  if (!b) return FDAS_ERR_INVALID;
+  if (seg_len) *seg_len = b->L;
+  if (z_bank) *z_bank = b->Z_bank;
+  if (units) *units = b->units;
+  if (segments_per_cta) *segments_per_cta = b->G;
+  return FDAS_OK;
+}
+
+int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int zstep, int tmpl_len,
+                        const int* seg_len_candidates, int n_candidates, const float* const* d_spectra,
+                        float* const* d_planes, fdas_stream_t stream, int* best_seg_len, float* ms_out) {
+  if (!seg_len_candidates || n_candidates < 1 || !best_seg_len) return FDAS_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float best = -1.f;
+  *best_seg_len = 0;
+  for (int c = 0; c < n_candidates; ++c) {
+    if (ms_out) ms_out[c] = -1.f;
+    fdas_batch* b = fdas_batch_create(count, n_bins, zmax, zstep, seg_len_candidates[c], tmpl_len);
+    if (!b) continue;   // this segment length cannot serve the batch (validation or no kernel)
+    int rc = fdas_batch_templates_build(b, stream);
+    if (rc == FDAS_OK) rc = fdas_batch_convolve_power(b, d_spectra, d_planes, 0, stream);   // warm-up
+    float ms = 0.f;
+    if (rc == FDAS_OK) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      const int reps = 3;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == FDAS_OK; ++r) rc = fdas::launch_batch(b->L, batch_params(b), b->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = FDAS_ERR_CUDA;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    if (rc == FDAS_OK) rc = fdas_batch_check(b, stream);
+    fdas_batch_destroy(b);
+    if (rc != FDAS_OK) return rc;
+    if (ms_out) ms_out[c] = ms;
+    if (best < 0.f || ms < best) {
+      best = ms;
+      *best_seg_len = seg_len_candidates[c];
+    }
+  }
+  return *best_seg_len ? FDAS_OK : FDAS_ERR_INVALID;
+}
+
+}  // extern "C"

@@ -394,11 +394,30 @@ struct TmemCfg {
   static_assert(SMEM <= 232448, "shared memory budget");
 };
 
+// Spectrum b holding flattened unit u (largest b with unit_base <= u).
+__device__ __forceinline__ int find_spectrum(const BatchParams& p, int64_t u) {
+  if (p.descs == nullptr) return 0;
+  int lo = 0, hi = p.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.descs[mid].unit_base <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ SpecDesc spectrum_desc(const BatchParams& p, int b) {
+  return p.descs == nullptr ? p.single : p.descs[b];
+}
+
 // NV: pass-2 output rows n1 < NV can hold valid outputs (NV >= ceil(V / N2)); rows n1 >= NV are
 // dropped at compile time, which also removes the butterfly halves that only feed them.
+//
+// Work: units (spectrum b, segment group g, template z) flattened over all spectra; each CTA
+// takes a contiguous equal range.  Segment s of spectrum b is brought in by one bulk copy of its
+// part inside [0, n_b) (cp.async.bulk) and the rest of the L-bin window is zero-filled by the
+// owning warp.
 template <class Cfg, int NV>
-__global__ void __launch_bounds__(256, 1)
-    fdas_convolve_tmem_kernel(const __grid_constant__ CUtensorMap spec_map, const ConvParams p) {
+__global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchParams p) {
   constexpr int L = Cfg::L, N1 = Cfg::N1, R = Cfg::R, G = Cfg::G, H2 = Cfg::H2, W = Cfg::W;
   extern __shared__ __align__(1024) unsigned char smem[];
   float2* sT = reinterpret_cast<float2*>(smem + Cfg::OFF_T);
@@ -443,12 +462,15 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tw_addr = tmem_row + Cfg::COL_TW;
   const uint32_t x_addr = tmem_row + Cfg::COL_X + (uint32_t)(warp >> 2) * (2 * Cfg::N2);
 
+  // template of CTA position i: bank row z_off_b + (u0 + i - unit_base_b) mod Z_b
   auto issue_template = [&](int64_t i) {
     const int slot = (int)(i % R);
-    const int64_t z = (u0 + i) % p.Z;
+    const int64_t u = u0 + i;
+    const SpecDesc d = spectrum_desc(p, find_spectrum(p, u));
+    const int64_t row = d.z_off + (u - d.unit_base) % d.Z;
     issued_pos[slot] = i;
     mbar_arrive_expect_tx(&full[slot], L * 8);
-    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)z * L, L * 8, &full[slot]);
+    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)row * L, L * 8, &full[slot]);
   };
   if (tid == 0) {
     const int64_t first = npos < R ? npos : R;
@@ -476,22 +498,46 @@ __global__ void __launch_bounds__(256, 1)
   int alive = 1;
   uint32_t seg_phase = 0;
   bool seg_in_flight = false;
-  const int64_t g_first = u0 / p.Z, g_last = (u1 - 1) / p.Z;
-  for (int64_t grp = g_first; grp <= g_last; ++grp) {
-    const int64_t a = (grp * p.Z > u0 ? grp * p.Z : u0) - u0;
-    const int64_t b = ((grp + 1) * p.Z < u1 ? (grp + 1) * p.Z : u1) - u0;
+  int64_t u = u0;
+  while (u < u1) {
+    // the segment group holding unit u
+    const int b = find_spectrum(p, u);
+    const SpecDesc d = spectrum_desc(p, b);
+    const int64_t grp = (u - d.unit_base) / d.Z;
+    const int64_t z_first = (u - d.unit_base) % d.Z;
+    const int64_t grp_end = d.unit_base + (grp + 1) * d.Z;
+    const int64_t a = u - u0;
+    const int64_t bpos = (grp_end < u1 ? grp_end : u1) - u0;
+    u = u0 + bpos;
     // every warp is done with its region (previous exchanges) before segments land in it
     alive = __syncthreads_and(alive && !*abort_flag);
     tmem_fence_after_sync();
     if (!alive) break;
     if (tid == 0) {
-      mbar_arrive_expect_tx(segbar, G * L * 8);
+      // a2: bulk copies of the in-range part of every segment of the group
+      uint32_t bytes = 0;
+      for (int j = 0; j < G; ++j) {
+        const int64_t x0 = (grp * G + j) * (int64_t)p.V - p.h;
+        const int64_t c0 = x0 > 0 ? x0 : 0;
+        const int64_t c1 = x0 + L < d.n_bins ? x0 + L : d.n_bins;
+        if (c1 > c0) bytes += (uint32_t)((c1 - c0) * 8);
+      }
+      mbar_arrive_expect_tx(segbar, bytes);
       for (int j = 0; j < G; ++j) {
         float2* dst = reinterpret_cast<float2*>(sReg + (size_t)(j / Cfg::F) * Cfg::REGION) + (size_t)(j % Cfg::F) * L;
         const int64_t x0 = (grp * G + j) * (int64_t)p.V - p.h;
-        for (int bx = 0; bx < L / Cfg::BOX; ++bx)
-          tma_load_1d(dst + bx * Cfg::BOX, &spec_map, (int32_t)(x0 + bx * Cfg::BOX), segbar);
+        const int64_t c0 = x0 > 0 ? x0 : 0;
+        const int64_t c1 = x0 + L < d.n_bins ? x0 + L : d.n_bins;
+        if (c1 > c0) bulk_g2s(dst + (c0 - x0), d.spec + c0, (uint32_t)((c1 - c0) * 8), segbar);
       }
+    }
+    {
+      // zeros outside [0, n_b) in this lane group's window
+      const int64_t x0 = (grp * G + warp * Cfg::F + gw) * (int64_t)p.V - p.h;
+      const int64_t lo = x0 < 0 ? (-x0 < L ? -x0 : L) : 0;                           // [0, lo) below 0
+      const int64_t hi = d.n_bins - x0 < L ? (d.n_bins - x0 > 0 ? d.n_bins - x0 : 0) : L;  // [hi, L) beyond n
+      for (int e = k1; e < L; e += N1)
+        if (e < lo || e >= hi) mySeg[e] = make_float2(0.f, 0.f);
     }
     seg_in_flight = true;
     alive = __syncthreads_and(mbar_wait(segbar, seg_phase) ? 1 : 0);
@@ -520,9 +566,9 @@ __global__ void __launch_bounds__(256, 1)
 
     const int64_t s = grp * G + warp * Cfg::F + gw;
     const int64_t segbase = s * (int64_t)p.V;
-    const int64_t lim64 = p.n_bins - segbase < (int64_t)p.V ? p.n_bins - segbase : (int64_t)p.V;
+    const int64_t lim64 = d.n_bins - segbase < (int64_t)p.V ? d.n_bins - segbase : (int64_t)p.V;
     const int lim = lim64 > 0 ? (int)lim64 : 0;
-    for (int64_t i = a; i < b; ++i) {
+    for (int64_t i = a; i < bpos; ++i) {
       const int slot = (int)(i % R);
       int ok = *abort_flag ? 0 : (mbar_wait(&full[slot], (uint32_t)((i / R) & 1)) ? 1 : 0);
       ok = __all_sync(0xffffffffu, ok);
@@ -530,7 +576,7 @@ __global__ void __launch_bounds__(256, 1)
         if (lane == 0) report_timeout(p.status, abort_flag);
         break;
       }
-      const int64_t z = (u0 + i) % p.Z;
+      const int64_t z = z_first + (i - a);
       const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
 
       // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
@@ -570,7 +616,7 @@ __global__ void __launch_bounds__(256, 1)
       // a5: inverse FFT
       fft_split_pairs<Cfg::N2, +1>(v);
       apply_twist_tmem<Cfg, false>(v, tw_addr);
-      float* row = p.plane + z * p.n_bins + segbase;
+      float* row = d.plane + z * d.n_bins + segbase;
       exchange_and_pass2<Cfg, +1>(v, myXb, k1, [&](auto, auto nn, const cp2& y) {
         // a6 + a7: keep n < V (and inside the spectrum), store |y|^2
         constexpr int n1 = decltype(nn)::value;
@@ -685,33 +731,69 @@ using Cfg1024 = ConvCfg<1024, 16, 2, 1>;
 using Cfg2048 = ConvCfg<2048, 32, 4, 1, 2>;
 
 template <class Cfg, int NV>
-static cudaError_t launch_tmem_nv(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
+static cudaError_t launch_tmem_nv(const BatchParams& p, int sm_count, cudaStream_t st) {
   auto kern = fdas_convolve_tmem_kernel<Cfg, NV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  ConvParams q = p;
-  const int64_t ngroups = (p.nseg + Cfg::G - 1) / Cfg::G;
-  q.units = ngroups * p.Z;
-  const int64_t grid = q.units < sm_count ? q.units : sm_count;
-  kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(*map, q);
+  const int64_t grid = p.units < sm_count ? p.units : sm_count;
+  kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
 // Smallest instantiated NV >= ceil(V / N2): N1*3/4, N1*7/8 or N1.
 template <class Cfg>
-static cudaError_t launch_tmem_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
+static cudaError_t launch_tmem_cfg(const BatchParams& p, int sm_count, cudaStream_t st) {
   const int rows = (p.V + Cfg::N2 - 1) / Cfg::N2;
-  if (rows <= Cfg::N1 * 3 / 4) return launch_tmem_nv<Cfg, Cfg::N1 * 3 / 4>(map, p, sm_count, st);
-  if (rows <= Cfg::N1 * 7 / 8) return launch_tmem_nv<Cfg, Cfg::N1 * 7 / 8>(map, p, sm_count, st);
-  return launch_tmem_nv<Cfg, Cfg::N1>(map, p, sm_count, st);
+  if (rows <= Cfg::N1 * 3 / 4) return launch_tmem_nv<Cfg, Cfg::N1 * 3 / 4>(p, sm_count, st);
+  if (rows <= Cfg::N1 * 7 / 8) return launch_tmem_nv<Cfg, Cfg::N1 * 7 / 8>(p, sm_count, st);
+  return launch_tmem_nv<Cfg, Cfg::N1>(p, sm_count, st);
+}
+
+int batch_segments_per_cta(int L) {
+  switch (L) {
+    case 512: return TmemCfg<512, 16>::G;
+    case 2048: return TmemCfg<2048, 32>::G;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t st) {
+  switch (L) {
+    case 512: return launch_tmem_cfg<TmemCfg<512, 16>>(p, sm_count, st);
+    case 2048: return launch_tmem_cfg<TmemCfg<2048, 32>>(p, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Single spectrum: the descriptor-driven kernel with an inline one-entry table where it exists.
+static cudaError_t launch_single_desc(int L, const ConvParams& p, int sm_count, cudaStream_t st) {
+  const int G = batch_segments_per_cta(L);
+  BatchParams q;
+  q.templates = p.templates;
+  q.twist = p.twist;
+  q.status = p.status;
+  q.descs = nullptr;
+  q.count = 1;
+  q.single.spec = p.spectrum;
+  q.single.plane = p.plane;
+  q.single.n_bins = p.n_bins;
+  q.single.nseg = p.nseg;
+  q.single.unit_base = 0;
+  q.single.ngroups = (p.nseg + G - 1) / G;
+  q.single.Z = p.Z;
+  q.single.z_off = 0;
+  q.units = q.single.ngroups * p.Z;
+  q.V = p.V;
+  q.h = p.h;
+  return launch_batch(L, q, sm_count, st);
 }
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
   switch (L) {
     case 256: return launch_conv_cfg<Cfg256>(map, p, sm_count, st);
-    case 512: return launch_tmem_cfg<TmemCfg<512, 16>>(map, p, sm_count, st);
+    case 512: return launch_single_desc(512, p, sm_count, st);
     case 1024: return launch_conv_cfg<Cfg1024>(map, p, sm_count, st);
-    case 2048: return launch_tmem_cfg<TmemCfg<2048, 32>>(map, p, sm_count, st);
+    case 2048: return launch_single_desc(2048, p, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }

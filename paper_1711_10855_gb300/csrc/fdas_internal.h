@@ -10,6 +10,7 @@ namespace fdas {
 
 // Parameters of the fused correlation kernel (steps a2..a7).
 struct ConvParams {
+  const float2* spectrum;   // n_bins complex64 (read by bulk copies in the descriptor-driven kernel)
   const float2* templates;  // Z x L template spectra, per-template layout of the IFFT's first pass
   const float2* twist;      // L inter-pass twiddles exp(+i 2pi n2 k1 / L), same layout
   float* plane;             // Z x n_bins output, row pitch n_bins
@@ -18,6 +19,30 @@ struct ConvParams {
   int64_t nseg;             // ceil(n_bins / V)
   int64_t units;            // (number of segment groups) x Z
   int Z, V, h;
+};
+
+// One spectrum of a batch, as the persistent kernel reads it (device table or inline).
+struct SpecDesc {
+  const float2* spec;       // n_bins complex64, 16-byte aligned
+  float* plane;             // Z x n_bins float32, row pitch n_bins
+  int64_t n_bins;
+  int64_t nseg;             // ceil(n_bins / V)
+  int64_t unit_base;        // first flattened (segment group, template) unit of this spectrum
+  int64_t ngroups;          // ceil(nseg / G), G = segments resident per CTA
+  int Z;                    // templates of this spectrum
+  int z_off;                // template-bank row of its first template
+};
+
+// Parameters of the descriptor-driven fused kernel (TMEM variant): one or many spectra.
+struct BatchParams {
+  const float2* templates;  // Z_bank x L template spectra (pair-major layout)
+  const float2* twist;      // L inter-pass twiddles (pair-major layout)
+  int* status;              // device status word (bit 0: a bounded wait gave up)
+  const SpecDesc* descs;    // device table of `count` spectra, or nullptr: use `single`
+  SpecDesc single;
+  int count;
+  int64_t units;            // total units over all spectra
+  int V, h;
 };
 
 // Parameters of the forward-transform-only kernel (steps a2 + a3, for tests).
@@ -34,6 +59,12 @@ struct SegParams {
 // twiddle table are stored in the layout of that decomposition (element k = k1 + N1*k2 at
 // ((k2/2)*N1 + k1)*2 + k2%2).
 int conv_group_threads(int L);
+
+// Segments resident per CTA of the descriptor-driven kernel for segment length L, or 0 if L has
+// no descriptor-driven kernel (then only the single-spectrum plan path serves it).
+int batch_segments_per_cta(int L);
+// Descriptor-driven launch (L with batch_segments_per_cta(L) > 0).
+cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t stream);
 
 // Launch helpers (defined in fdas_convolve.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_convolve(int L, const CUtensorMap* spec_map, const ConvParams& p, int sm_count,

@@ -98,6 +98,7 @@ extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, i
   rc = fdas::encode_spectrum_map(&map, d_spectrum, n_bins, L);
   if (rc != FDAS_OK) return rc;
   fdas::ConvParams q;
+  q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
   q.templates = templates;
   q.twist = twist;
   q.plane = d_plane;

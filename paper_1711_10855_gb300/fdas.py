@@ -24,7 +24,10 @@ ERRORS = {
 EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_templates_build",
             "fdas_convolve_power", "fdas_check", "fdas_destroy", "fdas_plan_dims",
             "fdas_template_taps", "fdas_template_spectrum", "fdas_segment_spectra",
-            "fdas_convolve_power_static", "fdas_selftest_wait_timeout"]
+            "fdas_convolve_power_static", "fdas_selftest_wait_timeout",
+            "fdas_batch_create", "fdas_batch_last_error", "fdas_batch_templates_build",
+            "fdas_batch_convolve_power", "fdas_batch_check", "fdas_batch_destroy", "fdas_batch_info",
+            "fdas_batch_autotune"]
 
 _lock = threading.Lock()
 _lib = None
@@ -67,6 +70,22 @@ def lib() -> ctypes.CDLL:
             L.fdas_template_spectrum.restype = i32
             L.fdas_segment_spectra.argtypes = [vp, vp, vp, vp]
             L.fdas_segment_spectra.restype = i32
+            L.fdas_batch_create.argtypes = [i32, vp, vp, i32, i32, i32]
+            L.fdas_batch_create.restype = vp
+            L.fdas_batch_last_error.argtypes = []
+            L.fdas_batch_last_error.restype = i32
+            L.fdas_batch_templates_build.argtypes = [vp, vp]
+            L.fdas_batch_templates_build.restype = i32
+            L.fdas_batch_convolve_power.argtypes = [vp, vp, vp, i32, vp]
+            L.fdas_batch_convolve_power.restype = i32
+            L.fdas_batch_check.argtypes = [vp, vp]
+            L.fdas_batch_check.restype = i32
+            L.fdas_batch_destroy.argtypes = [vp]
+            L.fdas_batch_destroy.restype = i32
+            L.fdas_batch_info.argtypes = [vp, vp, vp, vp, vp]
+            L.fdas_batch_info.restype = i32
+            L.fdas_batch_autotune.argtypes = [i32, vp, vp, i32, i32, vp, i32, vp, vp, vp, vp, vp]
+            L.fdas_batch_autotune.restype = i32
             L.fdas_selftest_wait_timeout.argtypes = [vp, i64, vp]
             L.fdas_selftest_wait_timeout.restype = i32
             L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
@@ -168,6 +187,90 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _i64_array(values):
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.int64))
+    return a, a.ctypes.data
+
+
+def _i32_array(values):
+    a = np.ascontiguousarray(np.asarray(values, dtype=np.int32))
+    return a, a.ctypes.data
+
+
+def _ptr_array(tensors):
+    a = np.ascontiguousarray(np.asarray([_ptr(t) for t in tensors], dtype=np.uint64))
+    return a, a.ctypes.data
+
+
+class Batch:
+    """fdas_batch: many spectra (uneven n_bins, per-spectrum zmax) in one persistent launch."""
+
+    def __init__(self, n_bins, zmax, zstep: int, seg_len: int, tmpl_len: int):
+        L = lib()
+        nb, nb_p = _i64_array(n_bins)
+        zm, zm_p = _i32_array(zmax)
+        if nb.size != zm.size:
+            raise ValueError("n_bins and zmax must have the same length")
+        h = L.fdas_batch_create(int(nb.size), nb_p, zm_p, int(zstep), int(seg_len), int(tmpl_len))
+        if not h:
+            raise FdasError(L.fdas_batch_last_error(), "fdas_batch_create")
+        self._h = h
+        self.n_bins, self.zmax = nb.copy(), zm.copy()
+        self.zstep, self.seg_len, self.tmpl_len = int(zstep), int(seg_len), int(tmpl_len)
+        self.n_z = 2 * (zm // int(zstep)) + 1
+        seg, zb, units, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        _check(L.fdas_batch_info(h, ctypes.byref(seg), ctypes.byref(zb), ctypes.byref(units), ctypes.byref(g)),
+               "fdas_batch_info")
+        self.z_bank, self.units, self.segments_per_cta = zb.value, units.value, g.value
+
+    def build_templates(self, stream=None):
+        _check(lib().fdas_batch_templates_build(self._h, _stream(stream)), "fdas_batch_templates_build")
+
+    def convolve_power(self, spectra, planes, use_graph: bool = False, stream=None):
+        if len(spectra) != self.n_bins.size or len(planes) != self.n_bins.size:
+            raise ValueError("one spectrum and one plane per batch entry")
+        sp, sp_p = _ptr_array(spectra)
+        pl, pl_p = _ptr_array(planes)
+        _check(lib().fdas_batch_convolve_power(self._h, sp_p, pl_p, 1 if use_graph else 0, _stream(stream)),
+               "fdas_batch_convolve_power")
+
+    def check(self, stream=None):
+        _check(lib().fdas_batch_check(self._h, _stream(stream)), "fdas_batch_check")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fdas_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(n_bins, zmax, zstep: int, tmpl_len: int, candidates, spectra, planes, stream=None):
+    """fdas_batch_autotune: the fastest segment length among `candidates` for this batch
+    (times one persistent launch per candidate on the given buffers). Returns (seg_len, ms list)."""
+    nb, nb_p = _i64_array(n_bins)
+    zm, zm_p = _i32_array(zmax)
+    cand, cand_p = _i32_array(candidates)
+    sp, sp_p = _ptr_array(spectra)
+    pl, pl_p = _ptr_array(planes)
+    best = ctypes.c_int()
+    ms = np.zeros(cand.size, dtype=np.float32)
+    _check(lib().fdas_batch_autotune(int(nb.size), nb_p, zm_p, int(zstep), int(tmpl_len), cand_p, int(cand.size),
+                                     sp_p, pl_p, _stream(stream), ctypes.byref(best), ms.ctypes.data),
+           "fdas_batch_autotune")
+    return best.value, [float(x) for x in ms]
 
 
 def convolve_power_static(n_bins: int, zmax: int, zstep: int, seg_len: int, tmpl_len: int,

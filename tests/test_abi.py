@@ -86,3 +86,27 @@ def test_no_device_is_an_error_not_a_fallback(lib, cuda_available):
     h = lib.fdas_plan_create(ctypes.c_int64(4096), 20, 2, 512, 64)
     assert not h
     assert lib.fdas_last_error() in (-6, -5)
+
+
+def test_batch_create_validation_without_device(lib):
+    import numpy as np
+    lib.fdas_batch_create.restype = ctypes.c_void_p
+    n = np.array([4096, 8192], dtype=np.int64)
+    z = np.array([20, 40], dtype=np.int32)
+
+    def create(count, nb, zm, zstep, L, m):
+        return lib.fdas_batch_create(count, ctypes.c_void_p(nb.ctypes.data), ctypes.c_void_p(zm.ctypes.data),
+                                     zstep, L, m)
+
+    assert not create(0, n, z, 2, 2048, 512)
+    assert lib.fdas_batch_last_error() == -1
+    assert not create(2, n, np.array([20, 41], dtype=np.int32), 2, 2048, 512)   # zmax % zstep
+    assert lib.fdas_batch_last_error() == -1
+    assert not create(2, np.array([4096, 8190], dtype=np.int64), z, 2, 2048, 512)   # n % 4
+    assert lib.fdas_batch_last_error() == -1
+    assert not create(2, n, z, 2, 1024, 256)   # no descriptor-driven kernel for L = 1024
+    assert lib.fdas_batch_last_error() == -1
+    assert lib.fdas_batch_destroy(None) == 0
+    assert lib.fdas_batch_check(None, None) == -1
+    assert lib.fdas_batch_templates_build(None, None) == -1
+    assert lib.fdas_batch_convolve_power(None, None, None, 0, None) == -1
