@@ -428,6 +428,13 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   unsigned* cnt = reinterpret_cast<unsigned*>(issued_pos + R);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(cnt + R);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cnt + R + 1);
+  // template-refill cursor (positions are issued in increasing order, one thread at a time)
+  struct IssueCursor {
+    int64_t u;          // unit of the next position to issue
+    int64_t spec_end;   // first unit of the next spectrum
+    int b, z, Z, z_off; // its spectrum, template index within it, that spectrum's Z and bank offset
+  };
+  IssueCursor* cur = reinterpret_cast<IssueCursor*>(smem + Cfg::OFF_BAR + 128);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gw = lane / N1, k1 = lane % N1;
@@ -462,17 +469,35 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   const uint32_t tw_addr = tmem_row + Cfg::COL_TW;
   const uint32_t x_addr = tmem_row + Cfg::COL_X + (uint32_t)(warp >> 2) * (2 * Cfg::N2);
 
-  // template of CTA position i: bank row z_off_b + (u0 + i - unit_base_b) mod Z_b
+  // Template of CTA position i (unit u0 + i): bank row z_off_b + (u - unit_base_b) mod Z_b.  The
+  // cursor walks units in order, so an issue costs a few shared-memory operations; a descriptor is
+  // read from global memory only when the walk enters the next spectrum.
   auto issue_template = [&](int64_t i) {
     const int slot = (int)(i % R);
-    const int64_t u = u0 + i;
-    const SpecDesc d = spectrum_desc(p, find_spectrum(p, u));
-    const int64_t row = d.z_off + (u - d.unit_base) % d.Z;
     issued_pos[slot] = i;
     mbar_arrive_expect_tx(&full[slot], L * 8);
-    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)row * L, L * 8, &full[slot]);
+    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)(cur->z_off + cur->z) * L, L * 8, &full[slot]);
+    cur->u += 1;
+    cur->z = cur->z + 1 == cur->Z ? 0 : cur->z + 1;
+    if (cur->u == cur->spec_end && cur->u < U) {
+      const int nb = cur->b + 1;
+      const SpecDesc dn = spectrum_desc(p, nb);
+      cur->b = nb;
+      cur->z = 0;
+      cur->Z = dn.Z;
+      cur->z_off = dn.z_off;
+      cur->spec_end = nb + 1 < p.count ? spectrum_desc(p, nb + 1).unit_base : U;
+    }
   };
   if (tid == 0) {
+    const int b0 = find_spectrum(p, u0);
+    const SpecDesc d0 = spectrum_desc(p, b0);
+    cur->u = u0;
+    cur->b = b0;
+    cur->Z = d0.Z;
+    cur->z_off = d0.z_off;
+    cur->z = (int)((u0 - d0.unit_base) % d0.Z);
+    cur->spec_end = b0 + 1 < p.count ? spectrum_desc(p, b0 + 1).unit_base : U;
     const int64_t first = npos < R ? npos : R;
     for (int64_t i = 0; i < first; ++i) issue_template(i);
   }
@@ -576,7 +601,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
         if (lane == 0) report_timeout(p.status, abort_flag);
         break;
       }
-      const int64_t z = z_first + (i - a);
+      const int64_t z = z_first + (int64_t)(i - a);
       const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
 
       // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
