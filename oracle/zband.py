@@ -1,0 +1,112 @@
+"""FP64 numpy statement of the z-band proposal network -- TEST INFRASTRUCTURE ONLY.
+
+The network reads a window of the z = 0 power spectrum (the plane's unaccelerated row, P[r] =
+|A_r|^2, Eq. 2 with z = 0) and predicts which templates of the z grid are worth correlating:
+
+    x      : (B, 1, W) window, normalised by its mean
+    h1     = relu(conv_k9(x;  W1 (32,1,9),  b1))        zero padding 4 ("same")
+    h2     = relu(conv_k9(h1; W2 (32,32,9), b2))
+    h3     = relu(conv_k9(h2; W3 (32,32,9), b3))
+    m[b,c] = max over the central positions [W/4, 3W/4) of h3[b,c,:]
+    logits = m @ Wl.T + bl                                (Wl: (Z, 32))
+    loss   = mean over (b, j) of BCE-with-logits(logits, target)
+
+conv_k9(x; W, b)[b, o, t] = b[o] + sum_{i,k} W[o, i, k] * x[b, i, t + k - 4].
+
+Only tests/ import this module.  The GPU implementation (csrc/fdas_zband.cu) shares nothing with it.
+Pins: tests/test_oracle_zband.py checks the forward against a loop-by-loop direct sum and the
+backward against central finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K = 9
+PAD = 4
+
+
+def conv_k9(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """(B, I, T) x (O, I, 9) -> (B, O, T), zero padding 4, FP64."""
+    B, I, T = x.shape
+    xp = np.zeros((B, I, T + 2 * PAD))
+    xp[:, :, PAD:PAD + T] = x
+    out = np.zeros((B, w.shape[0], T))
+    for k in range(K):
+        out += np.einsum("oi,bit->bot", w[:, :, k], xp[:, :, k:k + T])
+    return out + b[None, :, None]
+
+
+def conv_k9_backward(x, w, dout):
+    """Gradients of conv_k9 w.r.t. input, weights and bias."""
+    B, I, T = x.shape
+    xp = np.zeros((B, I, T + 2 * PAD))
+    xp[:, :, PAD:PAD + T] = x
+    dxp = np.zeros_like(xp)
+    dw = np.zeros_like(w)
+    for k in range(K):
+        dw[:, :, k] = np.einsum("bot,bit->oi", dout, xp[:, :, k:k + T])
+        dxp[:, :, k:k + T] += np.einsum("oi,bot->bit", w[:, :, k], dout)
+    return dxp[:, :, PAD:PAD + T], dw, dout.sum(axis=(0, 2))
+
+
+def normalise(window: np.ndarray) -> np.ndarray:
+    """Divide each window by its mean (power spectra of different lengths become comparable)."""
+    w = np.asarray(window, dtype=np.float64)
+    return w / np.maximum(w.mean(axis=-1, keepdims=True), 1e-30)
+
+
+def forward(params: dict, x: np.ndarray, keep: bool = False):
+    """params: W1,b1,W2,b2,W3,b3,Wl,bl (float arrays).  x: (B, W) normalised windows."""
+    h0 = np.asarray(x, dtype=np.float64)[:, None, :]
+    a1 = conv_k9(h0, params["W1"], params["b1"])
+    h1 = np.maximum(a1, 0.0)
+    a2 = conv_k9(h1, params["W2"], params["b2"])
+    h2 = np.maximum(a2, 0.0)
+    a3 = conv_k9(h2, params["W3"], params["b3"])
+    h3 = np.maximum(a3, 0.0)
+    T = h3.shape[2]
+    lo, hi = T // 4, 3 * T // 4
+    centre = h3[:, :, lo:hi]
+    arg = np.argmax(centre, axis=2) + lo          # first maximum
+    m = np.take_along_axis(h3, arg[:, :, None], axis=2)[:, :, 0]
+    logits = m @ params["Wl"].T + params["bl"][None, :]
+    if not keep:
+        return logits
+    return logits, dict(h0=h0, a1=a1, h1=h1, a2=a2, h2=h2, a3=a3, h3=h3, arg=arg, m=m)
+
+
+def bce_with_logits(logits: np.ndarray, target: np.ndarray) -> float:
+    """mean of max(l,0) - l*t + log(1 + exp(-|l|))"""
+    l = logits
+    return float(np.mean(np.maximum(l, 0) - l * target + np.log1p(np.exp(-np.abs(l)))))
+
+
+def loss_and_grads(params: dict, x: np.ndarray, target: np.ndarray):
+    logits, c = forward(params, x, keep=True)
+    loss = bce_with_logits(logits, target)
+    n = logits.size
+    dlog = (1.0 / (1.0 + np.exp(-logits)) - target) / n
+    g = {}
+    g["Wl"] = dlog.T @ c["m"]
+    g["bl"] = dlog.sum(axis=0)
+    dm = dlog @ params["Wl"]
+    dh3 = np.zeros_like(c["h3"])
+    B, C, _ = dh3.shape
+    dh3[np.arange(B)[:, None], np.arange(C)[None, :], c["arg"]] = dm
+    da3 = dh3 * (c["a3"] > 0)
+    dh2, g["W3"], g["b3"] = conv_k9_backward(c["h2"], params["W3"], da3)
+    da2 = dh2 * (c["a2"] > 0)
+    dh1, g["W2"], g["b2"] = conv_k9_backward(c["h1"], params["W2"], da2)
+    da1 = dh1 * (c["a1"] > 0)
+    _, g["W1"], g["b1"] = conv_k9_backward(c["h0"], params["W1"], da1)
+    return loss, g
+
+
+def init_params(n_out: int, seed: int = 0, channels: int = 32) -> dict:
+    rng = np.random.default_rng(seed)
+    def he(shape, fan_in):
+        return rng.standard_normal(shape) * np.sqrt(2.0 / fan_in)
+    return {"W1": he((channels, 1, K), K), "b1": np.zeros(channels),
+            "W2": he((channels, channels, K), channels * K), "b2": np.zeros(channels),
+            "W3": he((channels, channels, K), channels * K), "b3": np.zeros(channels),
+            "Wl": he((n_out, channels), channels), "bl": np.zeros(n_out)}
