@@ -1,21 +1,28 @@
 """FP64 numpy statement of the z-band proposal network -- TEST INFRASTRUCTURE ONLY.
 
-The network reads a window of the z = 0 power spectrum (the plane's unaccelerated row, P[r] =
-|A_r|^2, Eq. 2 with z = 0) and predicts which templates of the z grid are worth correlating:
+The network reads the z = 0 power spectrum (the plane's unaccelerated row: with z = 0 the
+template is a unit impulse, so Eq. 2 gives P[0][r] = |A_r|^2) and predicts which templates of
+the z grid are worth correlating near each block of bins.  The paper has no such network; this
+is the plain definition the CUDA kernels are checked against.
 
-    x      : (B, 1, W) window, normalised by its mean
-    h1     = relu(conv_k9(x;  W1 (32,1,9),  b1))        zero padding 4 ("same")
+    x_r    = min(|A_r|^2 / mean_r' |A_r'|^2, X_CAP)       whole-spectrum mean, cap 64
+    window w (width W, hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
+    h1     = relu(conv_k9(x;  W1 (32,1,9),  b1))        zero padding 4 ("same") at the window edge
     h2     = relu(conv_k9(h1; W2 (32,32,9), b2))
     h3     = relu(conv_k9(h2; W3 (32,32,9), b3))
-    m[b,c] = max over the central positions [W/4, 3W/4) of h3[b,c,:]
+    m[b,c] = max over the central positions [W/4, 3W/4) of h3[b,c,:]   (= bins of block w)
     logits = m @ Wl.T + bl                                (Wl: (Z, 32))
     loss   = mean over (b, j) of BCE-with-logits(logits, target)
 
 conv_k9(x; W, b)[b, o, t] = b[o] + sum_{i,k} W[o, i, k] * x[b, i, t + k - 4].
 
+The central positions' receptive field (+-12 bins) stays inside the window, so the logits of
+block w equal those of the same layers run over the whole zero-extended x sequence and pooled
+over [w*H, (w+1)*H) -- the form the fast inference kernel computes.
+
 Only tests/ import this module.  The GPU implementation (csrc/fdas_zband.cu) shares nothing with it.
-Pins: tests/test_oracle_zband.py checks the forward against a loop-by-loop direct sum and the
-backward against central finite differences.
+Pins: tests/test_oracle_zband.py (direct sums, finite differences, closed forms of Adam's first
+step, brute-force work lists).
 """
 from __future__ import annotations
 
@@ -49,10 +56,39 @@ def conv_k9_backward(x, w, dout):
     return dxp[:, :, PAD:PAD + T], dw, dout.sum(axis=(0, 2))
 
 
-def normalise(window: np.ndarray) -> np.ndarray:
-    """Divide each window by its mean (power spectra of different lengths become comparable)."""
-    w = np.asarray(window, dtype=np.float64)
-    return w / np.maximum(w.mean(axis=-1, keepdims=True), 1e-30)
+X_CAP = 64.0
+
+
+def power_x(spectrum: np.ndarray) -> np.ndarray:
+    """x_r = min(|A_r|^2 / mean |A|^2, X_CAP) in FP64 (spectrum: complex n-vector)."""
+    a = np.asarray(spectrum).astype(np.complex128)
+    p = a.real ** 2 + a.imag ** 2
+    mean = p.mean()
+    x = p / mean if mean > 0 else np.zeros_like(p)
+    return np.minimum(x, X_CAP)
+
+
+def windows(x: np.ndarray, window: int, hop: int, n_windows: int) -> np.ndarray:
+    """(n_windows, window): window w holds x at bins w*hop - window//4 + t, 0 outside [0, n)."""
+    n = x.size
+    out = np.zeros((n_windows, window))
+    for w in range(n_windows):
+        r0 = w * hop - window // 4
+        lo, hi = max(r0, 0), min(r0 + window, n)
+        if hi > lo:
+            out[w, lo - r0:hi - r0] = x[lo:hi]
+    return out
+
+
+def n_blocks(n_bins: int, window: int) -> int:
+    hop = window // 2
+    return -(-n_bins // hop)
+
+
+def block_logits(params: dict, spectrum: np.ndarray, window: int) -> np.ndarray:
+    """Logits of every block [w*H, (w+1)*H), H = window/2, of a whole spectrum."""
+    x = power_x(spectrum)
+    return forward(params, windows(x, window, window // 2, n_blocks(x.size, window)))
 
 
 def forward(params: dict, x: np.ndarray, keep: bool = False):
@@ -110,3 +146,28 @@ def init_params(n_out: int, seed: int = 0, channels: int = 32) -> dict:
             "W2": he((channels, channels, K), channels * K), "b2": np.zeros(channels),
             "W3": he((channels, channels, K), channels * K), "b3": np.zeros(channels),
             "Wl": he((n_out, channels), channels), "bl": np.zeros(n_out)}
+
+
+def adam_step(p, g, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1; returns (p, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def work_units(logits: np.ndarray, threshold: float, hop: int, group_bins: int, h: int, n_groups: int) -> np.ndarray:
+    """Ascending units g*Z + z: template z of segment group g (output bins [g*group_bins,
+    (g+1)*group_bins), input bins reaching h further on each side) is kept when a block w whose
+    bins [w*hop, (w+1)*hop) meet [g*group_bins - h, (g+1)*group_bins + h) has
+    sigmoid(logit[w, z]) >= threshold."""
+    nw, Z = logits.shape
+    keep = 1.0 / (1.0 + np.exp(-np.asarray(logits, dtype=np.float64))) >= threshold
+    units = []
+    for g in range(n_groups):
+        lo, hi = g * group_bins - h, (g + 1) * group_bins + h
+        for z in range(Z):
+            if any(keep[w, z] for w in range(nw) if w * hop < hi and (w + 1) * hop > lo):
+                units.append(g * Z + z)
+    return np.asarray(units, dtype=np.int64)

@@ -57,3 +57,78 @@ def test_pooling_window_is_the_centre_half():
     x = np.ones((1, 64))
     _, c = zband.forward(params, x, keep=True)
     assert np.all((c["arg"] >= 16) & (c["arg"] < 48))
+
+
+def test_power_x_closed_form_and_cap():
+    a = np.array([1.0, 1j, 2.0, 0.0])
+    np.testing.assert_allclose(zband.power_x(a), [2 / 3, 2 / 3, 8 / 3, 0.0], rtol=1e-15)
+    b = np.ones(1000, dtype=complex)
+    b[7] = 100.0                       # |A|^2 = 1e4, mean ~ 10.99 -> x ~ 910 -> capped
+    x = zband.power_x(b)
+    assert x[7] == zband.X_CAP
+    np.testing.assert_allclose(x[0], 1000.0 / (999.0 + 1e4), rtol=1e-15)
+    assert np.all(zband.power_x(np.zeros(8)) == 0.0)
+
+
+def test_windows_by_index_and_centre_halves_tile_the_spectrum():
+    rng = np.random.default_rng(4)
+    x = rng.random(50)
+    W, H = 16, 8
+    nw = zband.n_blocks(50, W)
+    assert nw == 7
+    win = zband.windows(x, W, H, nw)
+    for w in range(nw):
+        for t in range(W):
+            r = w * H - W // 4 + t
+            assert win[w, t] == (x[r] if 0 <= r < 50 else 0.0)
+    centre = np.concatenate([win[w, W // 4:3 * W // 4] for w in range(nw)])
+    np.testing.assert_array_equal(centre[:50], x)
+    assert np.all(centre[50:] == 0.0)
+
+
+def test_block_logits_equal_the_whole_sequence_network():
+    """The windowed definition equals the layers run once over the zero-extended sequence and
+    max-pooled per block (the receptive field of +-12 bins stays inside each window)."""
+    rng = np.random.default_rng(5)
+    n, W = 200, 64
+    H = W // 2
+    spec = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    params = zband.init_params(n_out=5, seed=6, channels=4)
+    for k in ("b1", "b2", "b3"):
+        params[k] = rng.standard_normal(params[k].shape) * 0.3    # nonzero biases: padding matters
+    x = zband.power_x(spec)
+    nb = zband.n_blocks(n, W)
+    E = 16                                  # zero extension on both sides (> 12)
+    total = nb * H + 2 * E
+    seq = np.zeros(total)
+    seq[E:E + n] = x
+    h = seq[None, None, :]
+    for wk, bk in (("W1", "b1"), ("W2", "b2"), ("W3", "b3")):
+        h = np.maximum(zband.conv_k9(h, params[wk], params[bk]), 0.0)
+    pooled = np.stack([h[0, :, E + w * H:E + (w + 1) * H].max(axis=1) for w in range(nb)])
+    want = pooled @ params["Wl"].T + params["bl"]
+    np.testing.assert_allclose(zband.block_logits(params, spec, W), want, rtol=1e-12, atol=1e-12)
+
+
+def test_adam_steps_move_by_lr_under_a_constant_gradient():
+    """With a constant gradient g the bias-corrected moments are g and g^2 at every step, so each
+    update is lr * g / (|g| + eps)."""
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal(20)
+    p0 = rng.standard_normal(20)
+    p, m, v = p0.copy(), np.zeros(20), np.zeros(20)
+    lr = 1e-2
+    for t in range(1, 6):
+        p, m, v = zband.adam_step(p, g, m, v, t, lr)
+        np.testing.assert_allclose(p, p0 - t * lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-12)
+
+
+def test_work_units_hand_computed():
+    # 4 blocks of hop 4: bins [0,4) [4,8) [8,12) [12,16); groups of 5 output bins, h = 1:
+    # group 0 reaches [-1, 6) -> blocks 0, 1; group 1 [4, 11) -> 1, 2; group 2 [9, 16) -> 2, 3
+    hi, lo = 3.0, -3.0
+    logits = np.array([[hi, lo], [lo, lo], [lo, hi], [lo, lo]])
+    got = zband.work_units(logits, 0.5, hop=4, group_bins=5, h=1, n_groups=3)
+    np.testing.assert_array_equal(got, [0 * 2 + 0, 1 * 2 + 1, 2 * 2 + 1])
+    assert zband.work_units(np.full((4, 2), lo), 0.5, 4, 5, 1, 3).size == 0
+    np.testing.assert_array_equal(zband.work_units(np.full((4, 2), hi), 0.5, 4, 5, 1, 3), np.arange(6))
