@@ -61,7 +61,7 @@ def workload(name: str, n_bins: int | None = None) -> synth.Workload:
 
 
 def algorithmic(w: synth.Workload, nseg: int) -> dict:
-    """Per-launch algorithmic bytes and flops (roofline section)."""
+    """Per-launch algorithmic bytes and flops of the correlation kernel."""
     n, Z, L, m = w.n_bins, w.n_z, w.seg_len, w.tmpl_len
     V = L - m
     bytes_plane = 4 * Z * n

@@ -63,7 +63,7 @@ enum fdas_status {
  * Create a plan for an n_bins-bin spectrum, the z grid -zmax..zmax step zstep, segment
  * length seg_len and template span tmpl_len (Section 1, Eq. 2; Section 2 overlap-and-save).
  *
- *   n_bins    >= 4 and a multiple of 4, < 2^32.
+ *   n_bins    >= 4 and a multiple of 4, <= 2^30.
  *   zmax      >= 0, zstep >= 1, zmax % zstep == 0; Z = 2*zmax/zstep + 1 <= 65535.
  *   seg_len   L, a power of two in [FDAS_MIN_SEG_LEN, FDAS_MAX_SEG_LEN].
  *   tmpl_len  m, a multiple of 4 with 4 <= m <= L/2 (so V = L - m >= L/2, V % 4 == 0).
@@ -112,9 +112,11 @@ int fdas_convolve_power(fdas_plan* plan, const float* d_spectrum, float* d_plane
                         fdas_stream_t stream);
 
 /*
- * Synchronise `stream` and report the plan's device status word: FDAS_OK, or FDAS_ERR_TIMEOUT
- * if a kernel of this plan abandoned a bounded wait (its outputs are then unspecified); the
- * word is cleared.  FDAS_ERR_CUDA if the synchronisation itself fails.
+ * Synchronise `stream` and report the plan's device status word: FDAS_OK, FDAS_ERR_TIMEOUT
+ * if a kernel of this plan abandoned a bounded wait (its outputs are then unspecified), or
+ * FDAS_ERR_INVALID if a work list given to fdas_convolve_power_units failed its device-side
+ * check (that call then wrote nothing); the word is cleared.  FDAS_ERR_CUDA if the
+ * synchronisation itself fails.
  */
 int fdas_check(fdas_plan* plan, fdas_stream_t stream);
 
@@ -201,6 +203,92 @@ int fdas_batch_info(const fdas_batch* batch, int* seg_len, int* z_bank, int64_t*
 int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int zstep, int tmpl_len,
                         const int* seg_len_candidates, int n_candidates, const float* const* d_spectra,
                         float* const* d_planes, fdas_stream_t stream, int* best_seg_len, float* ms_out);
+
+/* ---------------------------------------------------------------------------------------------
+ * Work lists.  The descriptor-driven kernel (seg_len 512 and 2048) groups
+ * fdas_plan_group_segments(plan) = G consecutive segments; a work unit is g*Z + z (segment
+ * group g, template z_idx).  fdas_convolve_power_units computes only the listed units (ascending,
+ * device int32 array, 4-byte aligned) and writes only their cells: the rows z of the bins
+ * [g*G*V, (g+1)*G*V) of each listed (g, z); every other cell of d_plane is left untouched.
+ * Each cell equals the one fdas_convolve_power writes.  The list is checked on the device
+ * (strictly increasing, every entry in [0, ceil(nseg/G)*Z)); a list that fails is not run
+ * and the next fdas_check() returns FDAS_ERR_INVALID.  Asynchronous, no allocation.
+ * FDAS_ERR_INVALID for a seg_len without that kernel.
+ * ------------------------------------------------------------------------------------------- */
+int fdas_plan_group_segments(const fdas_plan* plan);
+int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d_plane, const int32_t* d_units,
+                              int64_t n_units, fdas_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned z-band proposal (no counterpart in the paper): a 1-D convolutional network over the
+ * z = 0 power spectrum (the plane's z = 0 row, Eq. 2 with the unit-impulse template) that
+ * predicts, for each block of bins, which of Z templates are worth correlating there.
+ *
+ *   x_r    = min(|A_r|^2 / mean_r' |A_r'|^2, 64)   one scale for the whole spectrum
+ *   window w of width W (hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
+ *   three k = 9 convolutions, 32 channels, zero padding 4 at the window edge, ReLU;
+ *   the maximum of each channel over the central half [W/4, 3W/4) (= block [w*H, (w+1)*H));
+ *   a linear layer to Z logits; training loss: mean BCE-with-logits against 0/1 targets.
+ *
+ * Parameters are one FP32 vector: W1 [32][1][9], b1 [32], W2 [32][32][9], b2 [32],
+ * W3 [32][32][9], b3 [32], Wl [Z][32], bl [Z]; an FP16 copy is kept for inference.
+ * Training (FP32 forward, backward and Adam) and windowed inference run on the CUDA cores;
+ * fdas_zband_propose runs the layers once over a whole spectrum on the tensor cores.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct fdas_zband fdas_zband;
+
+/* window W: a multiple of 128 in [128, 65536]; n_out = Z in [1, 65535]; max_batch windows per
+ * call in [1, 65535].  Requires a compute capability 10.3 device (current device).  NULL on
+ * invalid arguments, another device, or allocation failure.  Parameters start at zero: set
+ * them before use.  Device memory ~ 5 * max_batch * 32 * W floats. */
+fdas_zband* fdas_zband_create(int window, int n_out, int max_batch);
+int fdas_zband_param_count(const fdas_zband* net);
+/* Host copies of the FP32 parameters (param_count floats).  Setting refreshes the FP16 copy and
+ * resets Adam (moments zero, step 0).  Both synchronise the device. */
+int fdas_zband_set_params(fdas_zband* net, const float* host_params);
+int fdas_zband_get_params(fdas_zband* net, float* host_params);
+/* Adam state for checkpoints: first and second moments (param_count floats each) and the step
+ * count.  Set after fdas_zband_set_params to resume training.  Synchronise the device. */
+int fdas_zband_get_adam(fdas_zband* net, float* host_m, float* host_v, int* host_step);
+int fdas_zband_set_adam(fdas_zband* net, const float* host_m, const float* host_v, int step);
+/* One Adam step (lr > 0; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on `batch` windows of
+ * x (device, batch x W floats, as fdas_zband_spectrum_windows makes them) with 0/1 targets
+ * (device, batch x Z).  The mean BCE loss is written to *host_loss when non-NULL (then
+ * synchronising `stream`).  Asynchronous otherwise. */
+int fdas_zband_train_step(fdas_zband* net, const float* d_windows, const float* d_targets, int batch, float lr,
+                          float* host_loss, fdas_stream_t stream);
+/* Gradients of the last train step (host, param_count floats; synchronises the device). */
+int fdas_zband_gradients(fdas_zband* net, float* host_grads);
+/* Logits (device, batch x Z) for windows of x on the CUDA cores (FP32 activations);
+ * half_weights != 0 uses the FP16 copy of the parameters. */
+int fdas_zband_predict(fdas_zband* net, const float* d_windows, int batch, int half_weights, float* d_logits,
+                       fdas_stream_t stream);
+/* Logits of every block of a whole spectrum, fused on the tensor cores: d_spectrum n_bins
+ * complex64 (device, 8-byte aligned), d_logits ceil(n_bins / H) x Z floats (device).  Row w is
+ * the network's output for window w (the same value fdas_zband_predict gives for that window,
+ * up to FP16 rounding of the activations).  Requires H = W/2 to be a multiple of 128 and at
+ * most 512.  Asynchronous, no allocation; uses the net's scratch, so calls on one net must not
+ * overlap.  A bounded device wait that gives up is reported by fdas_zband_check. */
+int fdas_zband_propose(fdas_zband* net, const float* d_spectrum, int64_t n_bins, float* d_logits,
+                       fdas_stream_t stream);
+/* Synchronise `stream`; FDAS_ERR_TIMEOUT if fdas_zband_propose abandoned a bounded wait (its
+ * logits are then unspecified), else FDAS_OK; clears the net's status word. */
+int fdas_zband_check(fdas_zband* net, fdas_stream_t stream);
+/* Windows of x for a whole spectrum (n_bins <= 2^30 complex64, 8-byte aligned): window w covers
+ * bins [w*hop - window/4, w*hop + 3*window/4), zeros outside [0, n_bins).  window a multiple of
+ * 4.  d_windows: n_windows x window floats.  Uses stream-ordered scratch allocations. */
+int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int window, int hop, float* d_windows,
+                                int64_t n_windows, fdas_stream_t stream);
+/* Work list from block logits (device, n_windows x Z): unit g*Z + z is kept when
+ * logit >= log(threshold / (1 - threshold)) (i.e. sigmoid(logit) >= threshold, 0 < threshold
+ * < 1) for template z in a block w whose bins [w*hop, (w+1)*hop) meet [g*group_bins - h,
+ * (g+1)*group_bins + h) (group_bins = G*V: the outputs of segment group g and the input bins
+ * its templates reach).  Writes the ascending list to d_units (room for n_groups*Z int32) and
+ * its length to *host_count (synchronises `stream`).  Uses stream-ordered scratch. */
+int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
+                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, int64_t* host_count,
+                          fdas_stream_t stream);
+int fdas_zband_destroy(fdas_zband* net);
 
 /*
  * Allocation-free variant of fdas_convolve_power, for callers that cannot allocate device

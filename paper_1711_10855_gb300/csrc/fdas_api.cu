@@ -363,6 +363,36 @@ int fdas_convolve_power(fdas_plan* p, const float* d_spectrum, float* d_plane, f
   return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
+int fdas_plan_group_segments(const fdas_plan* p) {
+  if (!p) return FDAS_ERR_INVALID;
+  const int G = fdas::batch_segments_per_cta(p->L);
+  return G > 0 ? G : FDAS_ERR_INVALID;
+}
+
+int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_units,
+                              int64_t n_units, fdas_stream_t stream) {
+  if (!p || !d_spectrum || !d_plane || !d_units || n_units < 1) return FDAS_ERR_INVALID;
+  if (!p->built) return FDAS_ERR_NOT_BUILT;
+  if (fdas::batch_segments_per_cta(p->L) == 0) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u) ||
+      (reinterpret_cast<uintptr_t>(d_units) & 3u))
+    return FDAS_ERR_ALIGN;
+  fdas::ConvParams q;
+  q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
+  q.templates = p->d_templates;
+  q.twist = p->d_twist;
+  q.plane = d_plane;
+  q.status = p->d_status;
+  q.n_bins = p->n_bins;
+  q.nseg = p->nseg;
+  q.units = 0;
+  q.Z = p->Z;
+  q.V = p->V;
+  q.h = p->h;
+  cudaError_t e = fdas::launch_units(p->L, q, d_units, n_units, p->sm_count, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
 int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fdas_stream_t stream) {
   if (!p || !d_spectrum || !d_out) return FDAS_ERR_INVALID;
   if (!p->built) return FDAS_ERR_NOT_BUILT;
@@ -390,7 +420,7 @@ int fdas_check(fdas_plan* p, fdas_stream_t stream) {
   if (cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
   if (status != 0) {
     cudaMemset(p->d_status, 0, sizeof(int));
-    return FDAS_ERR_TIMEOUT;
+    return (status & 1) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
   }
   return FDAS_OK;
 }

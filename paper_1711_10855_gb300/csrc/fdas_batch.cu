@@ -61,6 +61,7 @@ fdas::BatchParams batch_params(const fdas_batch* b) {
   q.descs = b->d_descs;
   q.count = b->count;
   q.units = b->units;
+  q.unit_list = nullptr;
   q.V = b->V;
   q.h = b->h;
   return q;

@@ -443,10 +443,14 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   float4* myXb = reinterpret_cast<float4*>(myRegion) + gw * Cfg::XGROUP;
 
   const int64_t U = p.units;
+  // flattened unit of list entry e (identity without a work list)
+  auto unit_at = [&](int64_t e) -> int64_t { return p.unit_list ? (int64_t)__ldg(p.unit_list + e) : e; };
   const int64_t u0 = (int64_t)blockIdx.x * U / gridDim.x;
   const int64_t u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
   const int64_t npos = u1 - u0;
   if (npos <= 0) return;
+  // a work list that failed its check (status bit 2, set by the preceding check kernel) is not run
+  if (p.unit_list && (*reinterpret_cast<volatile const int*>(p.status) & 2)) return;
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) {
@@ -475,8 +479,10 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   auto issue_template = [&](int64_t i) {
     const int slot = (int)(i % R);
     issued_pos[slot] = i;
+    const int64_t zrow = p.unit_list ? cur->z_off + unit_at(u0 + i) % cur->Z : cur->z_off + cur->z;
     mbar_arrive_expect_tx(&full[slot], L * 8);
-    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)(cur->z_off + cur->z) * L, L * 8, &full[slot]);
+    bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)zrow * L, L * 8, &full[slot]);
+    if (p.unit_list) return;   // single spectrum: the cursor's spectrum never changes
     cur->u += 1;
     cur->z = cur->z + 1 == cur->Z ? 0 : cur->z + 1;
     if (cur->u == cur->spec_end && cur->u < U) {
@@ -525,12 +531,19 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   bool seg_in_flight = false;
   int64_t u = u0;
   while (u < u1) {
-    // the segment group holding unit u
-    const int b = find_spectrum(p, u);
+    // the segment group holding entry u (a run of list entries with the same group)
+    const int64_t uu = unit_at(u);
+    const int b = find_spectrum(p, uu);
     const SpecDesc d = spectrum_desc(p, b);
-    const int64_t grp = (u - d.unit_base) / d.Z;
-    const int64_t z_first = (u - d.unit_base) % d.Z;
-    const int64_t grp_end = d.unit_base + (grp + 1) * d.Z;
+    const int64_t grp = (uu - d.unit_base) / d.Z;
+    const int64_t z_first = (uu - d.unit_base) % d.Z;
+    int64_t grp_end;
+    if (p.unit_list) {
+      grp_end = u + 1;
+      while (grp_end < u1 && unit_at(grp_end) / d.Z == grp) ++grp_end;
+    } else {
+      grp_end = d.unit_base + (grp + 1) * d.Z;
+    }
     const int64_t a = u - u0;
     const int64_t bpos = (grp_end < u1 ? grp_end : u1) - u0;
     u = u0 + bpos;
@@ -601,7 +614,8 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
         if (lane == 0) report_timeout(p.status, abort_flag);
         break;
       }
-      const int64_t z = z_first + (int64_t)(i - a);
+      // row of this position: consecutive templates without a list, the entry's own with one
+      const int64_t z = p.unit_list ? unit_at(u0 + i) % d.Z : z_first + (int64_t)(i - a);
       const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
 
       // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
@@ -808,6 +822,47 @@ static cudaError_t launch_single_desc(int L, const ConvParams& p, int sm_count, 
   q.single.Z = p.Z;
   q.single.z_off = 0;
   q.units = q.single.ngroups * p.Z;
+  q.unit_list = nullptr;
+  q.V = p.V;
+  q.h = p.h;
+  return launch_batch(L, q, sm_count, st);
+}
+
+// A work list is usable when its entries are strictly increasing and inside [0, limit): that
+// bounds every template row, segment and plane row the kernel touches.  Otherwise status bit 2.
+__global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limit, int* status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = units[e];
+    if (u < 0 || u >= limit || (e > 0 && (int64_t)units[e - 1] >= u)) atomicOr(status, 2);
+  }
+}
+
+cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, int64_t n_units, int sm_count,
+                         cudaStream_t st) {
+  const int G = batch_segments_per_cta(L);
+  if (G == 0 || n_units < 1) return cudaErrorInvalidValue;
+  const int64_t ngroups = (p.nseg + G - 1) / G;
+  {
+    const int64_t blocks = (n_units + 255) / 256;
+    const unsigned grid = (unsigned)(blocks < 4LL * sm_count ? blocks : 4LL * sm_count);
+    check_units_kernel<<<grid, 256, 0, st>>>(units, n_units, ngroups * p.Z, p.status);
+  }
+  BatchParams q;
+  q.templates = p.templates;
+  q.twist = p.twist;
+  q.status = p.status;
+  q.descs = nullptr;
+  q.count = 1;
+  q.single.spec = p.spectrum;
+  q.single.plane = p.plane;
+  q.single.n_bins = p.n_bins;
+  q.single.nseg = p.nseg;
+  q.single.unit_base = 0;
+  q.single.ngroups = ngroups;
+  q.single.Z = p.Z;
+  q.single.z_off = 0;
+  q.units = n_units;
+  q.unit_list = units;
   q.V = p.V;
   q.h = p.h;
   return launch_batch(L, q, sm_count, st);

@@ -41,7 +41,8 @@ struct BatchParams {
   const SpecDesc* descs;    // device table of `count` spectra, or nullptr: use `single`
   SpecDesc single;
   int count;
-  int64_t units;            // total units over all spectra
+  int64_t units;            // total units over all spectra (or entries of unit_list)
+  const int32_t* unit_list; // single spectrum only: ascending units g*Z + z to compute, or nullptr: all
   int V, h;
 };
 
@@ -65,6 +66,9 @@ int conv_group_threads(int L);
 int batch_segments_per_cta(int L);
 // Descriptor-driven launch (L with batch_segments_per_cta(L) > 0).
 cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t stream);
+// Single spectrum restricted to a work list of units g*Z + z (ascending).
+cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, int64_t n_units, int sm_count,
+                         cudaStream_t stream);
 
 // Launch helpers (defined in fdas_convolve.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_convolve(int L, const CUtensorMap* spec_map, const ConvParams& p, int sm_count,

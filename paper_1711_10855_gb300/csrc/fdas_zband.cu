@@ -1,0 +1,899 @@
+// fdas_zband.cu -- the learned z-band proposal (declared in include/fdas.h): a 1-D convolutional
+// network over the z = 0 power spectrum that predicts which templates of the z grid are worth
+// correlating near each block of bins, with hand-written training (FP32 forward, backward,
+// Adam) and inference (a fused tcgen05 kernel: FP16 weights and activations, FP32
+// accumulation), and the conversion of its proposals into a work list for the correlation
+// kernel.  The paper has no counterpart; the full search stays the reference against which
+// recall is measured.
+//
+// Network (window width Wd, hop Wd/2, C = 32 channels, k = 9, zero padding 4):
+//   x_r = min(|A_r|^2 / mean |A|^2, 64)   (one scale for the whole spectrum)
+//   window w = x over bins [w*hop - Wd/4, w*hop + 3Wd/4), 0 outside [0, n)
+//   a1 = conv(x; W1, b1), a2 = conv(relu(a1); W2, b2), a3 = conv(relu(a2); W3, b3)
+//   m[c] = max over t in [Wd/4, 3Wd/4) of relu(a3[c][t]),   logits = Wl m + bl  (Z outputs)
+//   loss = mean BCE-with-logits(logits, target)
+// The central positions' receptive field (+-12) stays inside the window, so the logits of
+// window w are those of the layers run once over the zero-extended x and max-pooled over the
+// block [w*hop, (w+1)*hop): the inference kernel computes that form, without the overlap.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "fdas.h"
+#include "fdas_device.cuh"
+#include "fdas_internal.h"
+
+namespace {
+
+constexpr int kC = 32;          // channels
+constexpr int kK = 9;           // kernel taps
+constexpr int kPad = 4;
+constexpr int kTile = 128;      // positions per conv block
+
+// Flat parameter layout (floats).
+struct Layout {
+  int W1, b1, W2, b2, W3, b3, Wl, bl, total;
+  explicit Layout(int Z) {
+    W1 = 0;
+    b1 = W1 + kC * 1 * kK;
+    W2 = b1 + kC;
+    b2 = W2 + kC * kC * kK;
+    W3 = b2 + kC;
+    b3 = W3 + kC * kC * kK;
+    Wl = b3 + kC;
+    bl = Wl + Z * kC;
+    total = bl + Z;
+  }
+};
+
+constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 / mean |A|^2, 64)
+constexpr int kSumBlocks = 512;  // fixed grid of the power reduction (deterministic order)
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// Whole-spectrum power sum in a fixed order: block b sums bins b*256 + t + k*512*256 in double
+// and writes partial[b]; power_scale_kernel folds the partials into scale = n / sum.
+__global__ void __launch_bounds__(256) power_partial_kernel(const float2* spec, int64_t n, double* partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x; r < n; r += (int64_t)kSumBlocks * 256) {
+    const float2 a = spec[r];
+    s += (double)fmaf(a.x, a.x, a.y * a.y);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kSumBlocks) power_scale_kernel(const double* partial, int64_t n, float* scale) {
+  __shared__ double red[kSumBlocks];
+  red[threadIdx.x] = partial[threadIdx.x];
+  __syncthreads();
+  for (int k = kSumBlocks / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *scale = red[0] > 0.0 ? (float)((double)n / red[0]) : 0.f;
+}
+
+__device__ __forceinline__ float power_x(const float2* spec, int64_t n, int64_t r, float scale) {
+  if (r < 0 || r >= n) return 0.f;
+  const float2 a = spec[r];
+  return fminf(fmaf(a.x, a.x, a.y * a.y) * scale, kXCap);
+}
+
+// Windows of x: window w covers bins [w*hop - Wd/4, w*hop + 3Wd/4), 0 outside [0, n).
+__global__ void spectrum_windows_kernel(const float2* spec, int64_t n, const float* scale, int Wd, int hop,
+                                        float* x) {
+  const int64_t w = blockIdx.x;
+  const int64_t r0 = w * hop - Wd / 4;
+  const float sc = *scale;
+  for (int t = threadIdx.x; t < Wd; t += blockDim.x) x[w * Wd + t] = power_x(spec, n, r0 + t, sc);
+}
+
+// pre[b][o][t] = bias[o] + sum_{i,k} W[o][i][k] * in(b, i, t + k - 4); in = x (CIN = 1) or
+// relu(prev pre-activation).  Block: 128 positions of one window, all 32 output channels;
+// thread (o = tid/8, t = tid%8 + 8j).
+template <int CIN>
+constexpr size_t conv_fwd_smem() { return sizeof(float) * ((size_t)CIN * (kTile + 2 * kPad) + (size_t)kC * CIN * kK); }
+
+template <int CIN, bool RELU_IN, typename WT>
+__global__ void __launch_bounds__(256) conv_fwd_kernel(const float* in, const WT* W, const WT* bias, float* pre,
+                                                       int Wd) {
+  extern __shared__ float dyn[];
+  float (*sIn)[kTile + 2 * kPad] = reinterpret_cast<float (*)[kTile + 2 * kPad]>(dyn);
+  float* sW = dyn + (size_t)CIN * (kTile + 2 * kPad);
+  const int b = blockIdx.y, t0 = blockIdx.x * kTile;
+  for (int idx = threadIdx.x; idx < kC * CIN * kK; idx += blockDim.x) sW[idx] = to_f(W[idx]);
+  for (int idx = threadIdx.x; idx < CIN * (kTile + 2 * kPad); idx += blockDim.x) {
+    const int i = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
+    const int t = t0 + tt - kPad;
+    float v = (t >= 0 && t < Wd) ? in[((size_t)b * CIN + i) * Wd + t] : 0.f;
+    if (RELU_IN) v = fmaxf(v, 0.f);
+    sIn[i][tt] = v;
+  }
+  __syncthreads();
+  const int o = threadIdx.x >> 3, tl = threadIdx.x & 7;
+  float acc[kTile / 8];
+  const float bo = to_f(bias[o]);
+#pragma unroll
+  for (int j = 0; j < kTile / 8; ++j) acc[j] = bo;
+  for (int i = 0; i < CIN; ++i) {
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+      const float w = sW[(o * CIN + i) * kK + k];
+#pragma unroll
+      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sIn[i][tl + 8 * j + k], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kTile / 8; ++j) pre[((size_t)b * kC + o) * Wd + t0 + tl + 8 * j] = acc[j];
+}
+
+// Pooling over the central half and the linear head: one block per window.
+template <typename WT>
+__global__ void pool_head_kernel(const float* a3, const WT* Wl, const WT* bl, int Wd, int Z, float* m_out,
+                                 int* arg_out, float* logits) {
+  const int b = blockIdx.x;
+  __shared__ float sm[kC];
+  const int lo = Wd / 4, hi = 3 * Wd / 4;
+  // 8 threads per channel, then combine (first maximum on ties)
+  const int c = threadIdx.x >> 3, l = threadIdx.x & 7;
+  float best = -1.f;
+  int barg = lo;
+  for (int t = lo + l; t < hi; t += 8) {
+    const float v = fmaxf(a3[((size_t)b * kC + c) * Wd + t], 0.f);
+    if (v > best) {
+      best = v;
+      barg = t;
+    }
+  }
+  for (int off = 4; off > 0; off >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, best, off, 8);
+    const int oa = __shfl_down_sync(0xffffffffu, barg, off, 8);
+    if (ov > best || (ov == best && oa < barg)) {
+      best = ov;
+      barg = oa;
+    }
+  }
+  if (l == 0) {
+    sm[c] = best;
+    if (m_out) m_out[b * kC + c] = best;
+    if (arg_out) arg_out[b * kC + c] = barg;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < Z; j += blockDim.x) {
+    float s = to_f(bl[j]);
+#pragma unroll 8
+    for (int cc = 0; cc < kC; ++cc) s = fmaf(to_f(Wl[j * kC + cc]), sm[cc], s);
+    logits[(size_t)b * Z + j] = s;
+  }
+}
+
+// dlog = (sigmoid(l) - target) / (B*Z); loss accumulated into *loss (sum of BCE terms / (B*Z)).
+__global__ void bce_grad_kernel(const float* logits, const float* target, int count, float* dlog, float* loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float term = 0.f;
+  if (i < count) {
+    const float l = logits[i], t = target[i];
+    dlog[i] = (1.f / (1.f + expf(-l)) - t) / (float)count;
+    term = fmaxf(l, 0.f) - l * t + log1pf(expf(-fabsf(l)));
+  }
+  for (int off = 16; off > 0; off >>= 1) term += __shfl_down_sync(0xffffffffu, term, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, term / (float)count);
+}
+
+// Head backward: dWl[j][c] = sum_b dlog[b][j] m[b][c], dbl[j] = sum_b dlog[b][j].
+__global__ void head_bwd_weights_kernel(const float* dlog, const float* m, int B, int Z, float* dWl, float* dbl) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Z * (kC + 1)) return;
+  const int j = idx / (kC + 1), c = idx % (kC + 1);
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += dlog[(size_t)b * Z + j] * (c < kC ? m[b * kC + c] : 1.f);
+  if (c < kC) dWl[j * kC + c] = s;
+  else dbl[j] = s;
+}
+
+// dm[b][c] = sum_j dlog[b][j] Wl[j][c]; then da3 = dm at the pooled position if a3 > 0 there.
+__global__ void head_bwd_data_kernel(const float* dlog, const float* Wl, const int* arg, const float* a3, int Z,
+                                     int Wd, float* da3) {
+  const int b = blockIdx.x, c = threadIdx.x;
+  if (c >= kC) return;
+  float s = 0.f;
+  for (int j = 0; j < Z; ++j) s = fmaf(dlog[(size_t)b * Z + j], Wl[j * kC + c], s);
+  const int t = arg[b * kC + c];
+  const size_t at = ((size_t)b * kC + c) * Wd + t;
+  da3[at] = a3[at] > 0.f ? s : 0.f;
+}
+
+// dIn_pre[b][i][t] = (prev_pre > 0) * sum_{o,k} W[o][i][k] dOut[b][o][t - k + 4].
+constexpr size_t kBwdDataSmem = sizeof(float) * ((size_t)kC * (kTile + 2 * kPad) + (size_t)kC * kC * kK);
+
+__global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* dout, const float* W, const float* prev_pre,
+                                                            float* din, int Wd) {
+  extern __shared__ float dyn[];
+  float (*sD)[kTile + 2 * kPad] = reinterpret_cast<float (*)[kTile + 2 * kPad]>(dyn);
+  float* sW = dyn + (size_t)kC * (kTile + 2 * kPad);
+  const int b = blockIdx.y, t0 = blockIdx.x * kTile;
+  for (int idx = threadIdx.x; idx < kC * kC * kK; idx += blockDim.x) sW[idx] = W[idx];
+  for (int idx = threadIdx.x; idx < kC * (kTile + 2 * kPad); idx += blockDim.x) {
+    const int o = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
+    const int t = t0 + tt - kPad;
+    sD[o][tt] = (t >= 0 && t < Wd) ? dout[((size_t)b * kC + o) * Wd + t] : 0.f;
+  }
+  __syncthreads();
+  const int i = threadIdx.x >> 3, tl = threadIdx.x & 7;
+  float acc[kTile / 8];
+#pragma unroll
+  for (int j = 0; j < kTile / 8; ++j) acc[j] = 0.f;
+  for (int o = 0; o < kC; ++o) {
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+      const float w = sW[(o * kC + i) * kK + k];
+      // dOut index t - k + 4 = (t0 + tl + 8j) - k + 4 -> tile offset tl + 8j - k + 8
+#pragma unroll
+      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sD[o][tl + 8 * j + 2 * kPad - k], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kTile / 8; ++j) {
+    const size_t at = ((size_t)b * kC + i) * Wd + t0 + tl + 8 * j;
+    din[at] = prev_pre[at] > 0.f ? acc[j] : 0.f;
+  }
+}
+
+// dW[o][i][k] += sum_{t in tile} in(b, i, t + k - 4) * dOut[b][o][t]; db[o] += sum dOut.
+// Block (tile, b); thread handles (o = tid/8) and i in {tid%8, tid%8 + 8, ...}.
+template <int CIN, bool RELU_IN>
+__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, const float* dout, int Wd, float* dW,
+                                                              float* db) {
+  __shared__ float sIn[CIN][kTile + 2 * kPad];
+  __shared__ float sD[kC][kTile];
+  const int b = blockIdx.y, t0 = blockIdx.x * kTile;
+  for (int idx = threadIdx.x; idx < CIN * (kTile + 2 * kPad); idx += blockDim.x) {
+    const int i = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
+    const int t = t0 + tt - kPad;
+    float v = (t >= 0 && t < Wd) ? in[((size_t)b * CIN + i) * Wd + t] : 0.f;
+    if (RELU_IN) v = fmaxf(v, 0.f);
+    sIn[i][tt] = v;
+  }
+  for (int idx = threadIdx.x; idx < kC * kTile; idx += blockDim.x) {
+    const int o = idx / kTile, tt = idx % kTile;
+    sD[o][tt] = dout[((size_t)b * kC + o) * Wd + t0 + tt];
+  }
+  __syncthreads();
+  const int o = threadIdx.x >> 3, l = threadIdx.x & 7;
+  for (int i = l; i < CIN; i += 8) {
+    float acc[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) acc[k] = 0.f;
+    for (int t = 0; t < kTile; ++t) {
+      const float d = sD[o][t];
+#pragma unroll
+      for (int k = 0; k < kK; ++k) acc[k] = fmaf(sIn[i][t + k], d, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kK; ++k) atomicAdd(&dW[(o * CIN + i) * kK + k], acc[k]);
+  }
+  if (l == 0) {
+    float s = 0.f;
+    for (int t = 0; t < kTile; ++t) s += sD[o][t];
+    atomicAdd(&db[o], s);
+  }
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_half_kernel(const float* p, __half* h, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) h[i] = __float2half_rn(p[i]);
+}
+
+// Proposal -> correlation work list.  Segment group g (G segments of V bins) is proposed for
+// template z if any window whose central bins [w*hop, (w+1)*hop) meet the bins the group's
+// outputs can draw on, [g*G*V - h, (g+1)*G*V + h), has sigmoid(logit_z) >= threshold.
+__global__ void group_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, int hop, int64_t group_bins,
+                                   int h, int n_groups, unsigned char* flags, int* counts) {
+  const int g = blockIdx.x;
+  const int64_t lo = (int64_t)g * group_bins - h, hi = (int64_t)(g + 1) * group_bins + h;
+  int w0 = (int)((lo > 0 ? lo : 0) / hop);
+  int w1 = (int)((hi + hop - 1) / hop);
+  if (w1 > n_win) w1 = n_win;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int z = threadIdx.x; z < Z; z += blockDim.x) {
+    unsigned char f = 0;
+    for (int w = w0; w < w1 && !f; ++w) f = logits[(size_t)w * Z + z] >= logit_thr;
+    flags[(size_t)g * Z + z] = f;
+    if (f) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) counts[g] = cnt;
+}
+
+// Exclusive scan of per-group counts (one block, sequential chunks) and the total.
+__global__ void scan_counts_kernel(const int* counts, int n_groups, int64_t* offsets, int64_t* total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t s = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    offsets[g] = s;
+    s += counts[g];
+  }
+  *total = s;
+}
+
+// units[offset_g + k] = g*Z + z for the k-th proposed z of group g (increasing z).
+__global__ void write_units_kernel(const unsigned char* flags, const int64_t* offsets, int Z, int32_t* units) {
+  const int g = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  int64_t o = offsets[g];
+  for (int z = 0; z < Z; ++z)
+    if (flags[(size_t)g * Z + z]) units[o++] = (int32_t)((int64_t)g * Z + z);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused inference over a whole spectrum on the tensor cores (tcgen05.mma kind::f16: FP16
+// weights and activations, FP32 accumulation in TMEM).  One CTA per SM walks blocks
+// w = blockIdx.x, blockIdx.x + gridDim.x, ...; block w owns output positions [w*hop, (w+1)*hop)
+// and recomputes the +-12-position halo its three layers need:
+//   x   at positions P0-12 .. (staged in shared memory, FP32)
+//   h1  at P0-8 + r, r < 128*T2 + 8      (layer 1 as an im2col GEMM: K = 9 taps padded to 16)
+//   h2  at P0-4 + r, r < hop + 8         (layer 2: T2 M-tiles of 128 positions)
+//   h3  at P0 + r,   r < hop             (layer 3: T3 = hop/128 M-tiles), max-pooled per channel
+// Activations sit in shared memory "chunk-planar": channel chunk j (8 channels, 16 B) of
+// position row r at plane j, offset 16*r.  A K-major no-swizzle operand whose rows are
+// positions is then one descriptor per (tap k, K-half c): start row + k, LBO = plane size,
+// SBO = 128 B -- the im2col of a k = 9 convolution costs no copies.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxHop = 512;
+constexpr int kT3max = kMaxHop / 128;
+constexpr int kT2max = kT3max + 1;
+constexpr int kT1max = kT2max + 1;
+constexpr int kNP1 = 128 * kT2max + 8;          // h1 rows (plane height)
+constexpr int kNP2 = 128 * kT2max;              // h2 rows (plane height)
+constexpr int kNA1 = 128 * kT1max;              // im2col rows of layer 1
+constexpr int kNX = kNA1 + 8;                   // staged x values
+constexpr uint32_t kPlaneH1 = kNP1 * 16, kPlaneH2 = kNP2 * 16, kPlaneA1 = kNA1 * 16;
+constexpr int kOffW1 = 0;                       // layer-1 weights: 2 K-chunks x 512 B
+constexpr int kOffW2 = kOffW1 + 1024;           // 9 taps x 4 K-chunks x 512 B
+constexpr int kOffW3 = kOffW2 + 9 * 2048;
+constexpr int kOffH1 = kOffW3 + 9 * 2048;       // also holds the staged x (dead before h1 is written)
+constexpr int kOffH2 = kOffH1 + 4 * kPlaneH1;   // also holds the layer-1 im2col (dead before h2)
+constexpr int kOffMisc = kOffH2 + 4 * kPlaneH2;
+constexpr int kProposeSmem = kOffMisc + 3 * kC * 4 + kC * 4 + 16 + 16;
+constexpr uint32_t kIdesc = fdas::umma_idesc_f16(128, kC);
+constexpr uint32_t kTmemCols = 256;             // one layer's accumulators at a time (<= 6 x 32 columns)
+static_assert(2 * kPlaneA1 <= 4 * kPlaneH2, "im2col must fit in the h2 planes");
+static_assert(kNX * 4 <= (int)(4 * kPlaneH1), "staged x must fit in the h1 planes");
+static_assert(32 * kT1max <= (int)kTmemCols, "accumulators must fit the TMEM allocation");
+static_assert(kProposeSmem <= 227 * 1024, "shared memory");
+
+struct ProposeParams {
+  const float2* spec;
+  int64_t n;
+  const float* scale;       // n / sum |A|^2 (device scalar)
+  const __half* w;          // FP16 parameter vector (Layout order)
+  int oW1, ob1, oW2, ob2, oW3, ob3, oWl, obl;
+  int Z, hop;
+  int64_t n_blocks;
+  float* logits;            // n_blocks x Z
+  int* status;              // bit 0: a bounded wait gave up
+};
+
+// B operand (weights) of one tap in the K-major no-swizzle layout: rows o (N = 32), K = in-ch.
+__device__ __forceinline__ int wb_off(int o, int i) { return (i >> 3) * 512 + (o >> 3) * 128 + (o & 7) * 16 + (i & 7) * 2; }
+
+__global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) {
+  using namespace fdas;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __half* sW1 = reinterpret_cast<__half*>(sm + kOffW1);
+  __half* sW2 = reinterpret_cast<__half*>(sm + kOffW2);
+  __half* sW3 = reinterpret_cast<__half*>(sm + kOffW3);
+  float* sX = reinterpret_cast<float*>(sm + kOffH1);
+  unsigned char* sH1 = sm + kOffH1;
+  unsigned char* sH2 = sm + kOffH2;
+  unsigned char* sA1 = sm + kOffH2;
+  float* sBias = reinterpret_cast<float*>(sm + kOffMisc);            // b1, b2, b3
+  unsigned* sMax = reinterpret_cast<unsigned*>(sBias + 3 * kC);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sMax + kC);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, half = warp >> 2;
+  // weights into the B layouts (FP16), biases as FP32 values of the FP16 copy
+  for (int idx = tid; idx < kC * 16; idx += 256) {
+    const int o = idx >> 4, k = idx & 15;
+    sW1[wb_off(o, k) / 2] = k < kK ? p.w[p.oW1 + o * kK + k] : __float2half_rn(0.f);
+  }
+  for (int idx = tid; idx < kK * kC * kC; idx += 256) {
+    const int k = idx / (kC * kC), o = (idx / kC) % kC, i = idx % kC;
+    sW2[k * 1024 + wb_off(o, i) / 2] = p.w[p.oW2 + (o * kC + i) * kK + k];
+    sW3[k * 1024 + wb_off(o, i) / 2] = p.w[p.oW3 + (o * kC + i) * kK + k];
+  }
+  if (tid < kC) {
+    sBias[tid] = __half2float(p.w[p.ob1 + tid]);
+    sBias[kC + tid] = __half2float(p.w[p.ob2 + tid]);
+    sBias[2 * kC + tid] = __half2float(p.w[p.ob3 + tid]);
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, kTmemCols);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tm = *tslot;
+  const uint32_t tm_lane = tm + ((uint32_t)(32 * q) << 16);
+  const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
+  const uint32_t aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aA1 = smem_u32(sA1);
+  const float sc = *p.scale;
+  const int T3 = p.hop / 128, T2 = T3 + 1, T1 = T2 + 1;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // wait for the MMAs committed last; every thread, bounded
+  auto wait_mma = [&]() -> bool {
+    const int good = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    phase ^= 1u;
+    tmem_fence_after_sync();
+    return good != 0;
+  };
+  // accumulator tile t (lanes = rows 128t + 32q + lane) + bias -> relu -> FP16 planes, rows < limit
+  auto store_layer = [&](int ntiles, int limit, const float* bias, unsigned char* dst, uint32_t plane) {
+    for (int t = half; t < ntiles; t += 2) {
+      float a[16], b[16];
+      tmem_ld16(tm_lane + 32 * t, a);
+      tmem_ld16(tm_lane + 32 * t + 16, b);
+      tmem_wait_ld();
+      const int r = 128 * t + 32 * q + lane;
+      if (r < limit) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          __half2 h[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 8 * j + 2 * e;
+            const float v0 = c < 16 ? a[c] : b[c - 16], v1 = c + 1 < 16 ? a[c + 1] : b[c - 15];
+            h[e] = __floats2half2_rn(fmaxf(v0 + bias[c], 0.f), fmaxf(v1 + bias[c + 1], 0.f));
+          }
+          *reinterpret_cast<uint4*>(dst + j * plane + r * 16) = *reinterpret_cast<uint4*>(h);
+        }
+      }
+    }
+  };
+  // one k = 9 convolution layer: ntiles M-tiles, A rows start at 128t + k in the source planes
+  auto issue_conv = [&](int ntiles, uint32_t src, uint32_t plane, uint32_t wts) {
+    for (int t = 0; t < ntiles; ++t)
+      for (int k = 0; k < kK; ++k)
+        for (int c = 0; c < 2; ++c)
+          umma_f16(tm + 32 * t, umma_desc(src + (uint32_t)(128 * t + k) * 16 + 2 * c * plane, plane, 128),
+                   umma_desc(wts + k * 2048 + c * 1024, 512, 128), kIdesc, (k | c) != 0);
+    umma_commit(bar);
+  };
+
+  for (int64_t w = blockIdx.x; w < p.n_blocks; w += gridDim.x) {
+    const int64_t P0 = w * p.hop;
+    for (int j = tid; j < 128 * T1 + 8; j += 256) sX[j] = power_x(p.spec, p.n, P0 - 12 + j, sc);
+    if (tid < kC) sMax[tid] = 0u;
+    __syncthreads();
+    // layer-1 im2col: row r (position P0-8+r) = x[r .. r+8], zero for K in [9, 16)
+    for (int r = tid; r < 128 * T1; r += 256) {
+      __half2 h[8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(sX[r + 2 * e], sX[r + 2 * e + 1]);
+      h[4] = __floats2half2_rn(sX[r + 8], 0.f);
+      h[5] = h[6] = h[7] = __floats2half2_rn(0.f, 0.f);
+      *reinterpret_cast<uint4*>(sA1 + r * 16) = *reinterpret_cast<uint4*>(&h[0]);
+      *reinterpret_cast<uint4*>(sA1 + kPlaneA1 + r * 16) = *reinterpret_cast<uint4*>(&h[4]);
+    }
+    fence_proxy_async_smem();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (tid == 0) {
+      for (int t = 0; t < T1; ++t)
+        umma_f16(tm + 32 * t, umma_desc(aA1 + (uint32_t)(128 * t) * 16, kPlaneA1, 128), umma_desc(aW1, 512, 128),
+                 kIdesc, 0u);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+    store_layer(T1, 128 * T2 + 8, sBias, sH1, kPlaneH1);
+    fence_proxy_async_smem();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (tid == 0) issue_conv(T2, aH1, kPlaneH1, aW2);
+    if (!(ok = wait_mma())) break;
+    store_layer(T2, p.hop + 8, sBias + kC, sH2, kPlaneH2);
+    fence_proxy_async_smem();
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (tid == 0) issue_conv(T3, aH2, kPlaneH2, aW3);
+    if (!(ok = wait_mma())) break;
+    // layer 3: relu(acc + b3), channel maxima over the block (non-negative floats order as unsigned)
+    for (int t = half; t < T3; t += 2) {
+      float a[16], b[16];
+      tmem_ld16(tm_lane + 32 * t, a);
+      tmem_ld16(tm_lane + 32 * t + 16, b);
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        const float v = fmaxf((c < 16 ? a[c] : b[c - 16]) + sBias[2 * kC + c], 0.f);
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+        if (lane == c) atomicMax(&sMax[c], m);
+      }
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    // head: logits[w][j] = bl[j] + sum_c Wl[j][c] m[c]  (FP16 weights, FP32 sums)
+    for (int j = tid; j < p.Z; j += 256) {
+      float s = __half2float(p.w[p.obl + j]);
+      const __half* wl = p.w + p.oWl + (size_t)j * kC;
+#pragma unroll 8
+      for (int c = 0; c < kC; ++c) s = fmaf(__half2float(wl[c]), __uint_as_float(sMax[c]), s);
+      p.logits[w * p.Z + j] = s;
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(p.status, 1);
+      (void)mbar_wait(bar, phase ^ 1u);   // bounded wait for the MMAs still in flight
+    }
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tm, kTmemCols);
+}
+
+}  // namespace
+
+struct fdas_zband {
+  int Wd = 0, Z = 0, max_batch = 0, sm_count = 0;
+  Layout lay{0};
+  float* p = nullptr;        // FP32 master parameters
+  __half* ph = nullptr;      // FP16 copy for inference
+  float* g = nullptr;        // gradients
+  float* m = nullptr;        // Adam moments
+  float* v = nullptr;
+  float* a1 = nullptr;       // pre-activations [B][C][Wd]
+  float* a2 = nullptr;
+  float* a3 = nullptr;
+  float* d1 = nullptr;       // gradient buffers [B][C][Wd]
+  float* d2 = nullptr;
+  float* pooled = nullptr;   // [B][C]
+  int* arg = nullptr;        // [B][C]
+  float* logits = nullptr;   // [B][Z]
+  float* dlog = nullptr;     // [B][Z]
+  float* loss = nullptr;     // device scalar
+  double* partial = nullptr; // power reduction partials [kSumBlocks]
+  float* scale = nullptr;    // n / sum |A|^2
+  int* status = nullptr;     // bit 0: a bounded wait of the inference kernel gave up
+  int step = 0;
+};
+
+namespace {
+void free_zband(fdas_zband* z) {
+  void* ptrs[] = {z->p,  z->ph,     z->g,   z->m,      z->v,    z->a1,   z->a2,      z->a3,    z->d1,
+                  z->d2, z->pooled, z->arg, z->logits, z->dlog, z->loss, z->partial, z->scale, z->status};
+  for (void* q : ptrs) cudaFree(q);
+  delete z;
+}
+
+// Layers 1..3, pooling and head on B windows `in` (FP32 activations; FP32 or FP16 weights).
+cudaError_t forward(fdas_zband* z, const float* in, int B, bool half_weights, cudaStream_t st) {
+  const Layout& L = z->lay;
+  const dim3 grid(z->Wd / kTile, B);
+  if (half_weights) {
+    const __half* h = z->ph;
+    conv_fwd_kernel<1, false, __half><<<grid, 256, conv_fwd_smem<1>(), st>>>(in, h + L.W1, h + L.b1, z->a1, z->Wd);
+    conv_fwd_kernel<kC, true, __half><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a1, h + L.W2, h + L.b2, z->a2, z->Wd);
+    conv_fwd_kernel<kC, true, __half><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a2, h + L.W3, h + L.b3, z->a3, z->Wd);
+    pool_head_kernel<__half><<<B, 256, 0, st>>>(z->a3, h + L.Wl, h + L.bl, z->Wd, z->Z, z->pooled, z->arg, z->logits);
+  } else {
+    const float* p = z->p;
+    conv_fwd_kernel<1, false, float><<<grid, 256, conv_fwd_smem<1>(), st>>>(in, p + L.W1, p + L.b1, z->a1, z->Wd);
+    conv_fwd_kernel<kC, true, float><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a1, p + L.W2, p + L.b2, z->a2, z->Wd);
+    conv_fwd_kernel<kC, true, float><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a2, p + L.W3, p + L.b3, z->a3, z->Wd);
+    pool_head_kernel<float><<<B, 256, 0, st>>>(z->a3, p + L.Wl, p + L.bl, z->Wd, z->Z, z->pooled, z->arg, z->logits);
+  }
+  return cudaGetLastError();
+}
+
+// scale = n / sum |A|^2 into `scale` (fixed reduction order).
+void launch_power_scale(const float2* spec, int64_t n, double* partial, float* scale, cudaStream_t st) {
+  power_partial_kernel<<<kSumBlocks, 256, 0, st>>>(spec, n, partial);
+  power_scale_kernel<<<1, kSumBlocks, 0, st>>>(partial, n, scale);
+}
+}  // namespace
+
+extern "C" {
+
+fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
+  if (window < kTile || window % kTile != 0 || window > (1 << 16) || n_out < 1 || n_out > 65535 || max_batch < 1 ||
+      max_batch > 65535)
+    return nullptr;
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || major != 10 || minor != 3) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaFuncSetAttribute(conv_fwd_kernel<kC, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_fwd_smem<kC>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_fwd_kernel<kC, true, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_fwd_smem<kC>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_bwd_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdDataSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  fdas_zband* z = new (std::nothrow) fdas_zband();
+  if (!z) return nullptr;
+  z->Wd = window;
+  z->Z = n_out;
+  z->max_batch = max_batch;
+  z->sm_count = sms;
+  z->lay = Layout(n_out);
+  const size_t P = (size_t)z->lay.total, B = (size_t)max_batch, act = B * kC * (size_t)window;
+  bool ok = cudaMalloc(&z->p, P * 4) == cudaSuccess && cudaMalloc(&z->ph, P * 2) == cudaSuccess &&
+            cudaMalloc(&z->g, P * 4) == cudaSuccess && cudaMalloc(&z->m, P * 4) == cudaSuccess &&
+            cudaMalloc(&z->v, P * 4) == cudaSuccess && cudaMalloc(&z->a1, act * 4) == cudaSuccess &&
+            cudaMalloc(&z->a2, act * 4) == cudaSuccess && cudaMalloc(&z->a3, act * 4) == cudaSuccess &&
+            cudaMalloc(&z->d1, act * 4) == cudaSuccess && cudaMalloc(&z->d2, act * 4) == cudaSuccess &&
+            cudaMalloc(&z->pooled, B * kC * 4) == cudaSuccess && cudaMalloc(&z->arg, B * kC * 4) == cudaSuccess &&
+            cudaMalloc(&z->logits, B * (size_t)n_out * 4) == cudaSuccess &&
+            cudaMalloc(&z->dlog, B * (size_t)n_out * 4) == cudaSuccess && cudaMalloc(&z->loss, 4) == cudaSuccess &&
+            cudaMalloc(&z->partial, kSumBlocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&z->scale, 4) == cudaSuccess && cudaMalloc(&z->status, 4) == cudaSuccess;
+  if (!ok || cudaMemset(z->p, 0, P * 4) != cudaSuccess || cudaMemset(z->ph, 0, P * 2) != cudaSuccess ||
+      cudaMemset(z->m, 0, P * 4) != cudaSuccess || cudaMemset(z->v, 0, P * 4) != cudaSuccess ||
+      cudaMemset(z->status, 0, 4) != cudaSuccess) {
+    cudaGetLastError();
+    free_zband(z);
+    return nullptr;
+  }
+  return z;
+}
+
+int fdas_zband_param_count(const fdas_zband* z) { return z ? z->lay.total : FDAS_ERR_INVALID; }
+
+int fdas_zband_set_params(fdas_zband* z, const float* host_params) {
+  if (!z || !host_params) return FDAS_ERR_INVALID;
+  const int P = z->lay.total;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(z->p, host_params, (size_t)P * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  to_half_kernel<<<(P + 255) / 256, 256>>>(z->p, z->ph, P);
+  cudaMemset(z->m, 0, (size_t)P * 4);
+  cudaMemset(z->v, 0, (size_t)P * 4);
+  z->step = 0;
+  return cudaDeviceSynchronize() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_zband_get_params(fdas_zband* z, float* host_params) {
+  if (!z || !host_params) return FDAS_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
+  return cudaMemcpy(host_params, z->p, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? FDAS_OK
+             : FDAS_ERR_CUDA;
+}
+
+int fdas_zband_get_adam(fdas_zband* z, float* host_m, float* host_v, int* host_step) {
+  if (!z || !host_m || !host_v || !host_step) return FDAS_ERR_INVALID;
+  const size_t bytes = (size_t)z->lay.total * 4;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(host_m, z->m, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(host_v, z->v, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  *host_step = z->step;
+  return FDAS_OK;
+}
+
+int fdas_zband_set_adam(fdas_zband* z, const float* host_m, const float* host_v, int step) {
+  if (!z || !host_m || !host_v || step < 0) return FDAS_ERR_INVALID;
+  const size_t bytes = (size_t)z->lay.total * 4;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(z->m, host_m, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(z->v, host_v, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  z->step = step;
+  return FDAS_OK;
+}
+
+int fdas_zband_train_step(fdas_zband* z, const float* d_windows, const float* d_targets, int batch, float lr,
+                          float* host_loss, fdas_stream_t stream) {
+  if (!z || !d_windows || !d_targets || batch < 1 || batch > z->max_batch || !(lr > 0.f)) return FDAS_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Layout& L = z->lay;
+  const int B = batch, Wd = z->Wd, Z = z->Z, P = L.total;
+  if (forward(z, d_windows, B, false, st) != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaMemsetAsync(z->loss, 0, 4, st);
+  cudaMemsetAsync(z->g, 0, (size_t)P * 4, st);
+  bce_grad_kernel<<<(B * Z + 255) / 256, 256, 0, st>>>(z->logits, d_targets, B * Z, z->dlog, z->loss);
+  head_bwd_weights_kernel<<<(Z * (kC + 1) + 255) / 256, 256, 0, st>>>(z->dlog, z->pooled, B, Z, z->g + L.Wl,
+                                                                       z->g + L.bl);
+  const size_t act = (size_t)B * kC * Wd;
+  cudaMemsetAsync(z->d1, 0, act * 4, st);
+  head_bwd_data_kernel<<<B, kC, 0, st>>>(z->dlog, z->p + L.Wl, z->arg, z->a3, Z, Wd, z->d1);   // da3
+  const dim3 grid(Wd / kTile, B);
+  conv_bwd_weight_kernel<kC, true><<<grid, 256, 0, st>>>(z->a2, z->d1, Wd, z->g + L.W3, z->g + L.b3);
+  conv_bwd_data_kernel<<<grid, 256, kBwdDataSmem, st>>>(z->d1, z->p + L.W3, z->a2, z->d2, Wd);   // da2
+  conv_bwd_weight_kernel<kC, true><<<grid, 256, 0, st>>>(z->a1, z->d2, Wd, z->g + L.W2, z->g + L.b2);
+  conv_bwd_data_kernel<<<grid, 256, kBwdDataSmem, st>>>(z->d2, z->p + L.W2, z->a1, z->d1, Wd);   // da1
+  conv_bwd_weight_kernel<1, false><<<grid, 256, 0, st>>>(d_windows, z->d1, Wd, z->g + L.W1, z->g + L.b1);
+  z->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)z->step), c2 = 1.f - powf(b2, (float)z->step);
+  adam_kernel<<<(P + 255) / 256, 256, 0, st>>>(z->p, z->g, z->m, z->v, P, lr, b1, b2, 1e-8f, c1, c2);
+  to_half_kernel<<<(P + 255) / 256, 256, 0, st>>>(z->p, z->ph, P);
+  if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;
+  if (host_loss) {
+    if (cudaMemcpyAsync(host_loss, z->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+  }
+  return FDAS_OK;
+}
+
+int fdas_zband_gradients(fdas_zband* z, float* host_grads) {
+  if (!z || !host_grads) return FDAS_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
+  return cudaMemcpy(host_grads, z->g, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? FDAS_OK
+             : FDAS_ERR_CUDA;
+}
+
+int fdas_zband_predict(fdas_zband* z, const float* d_windows, int batch, int half_weights, float* d_logits,
+                       fdas_stream_t stream) {
+  if (!z || !d_windows || !d_logits || batch < 1) return FDAS_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int b0 = 0; b0 < batch; b0 += z->max_batch) {
+    const int B = batch - b0 < z->max_batch ? batch - b0 : z->max_batch;
+    if (forward(z, d_windows + (size_t)b0 * z->Wd, B, half_weights != 0, st) != cudaSuccess) return FDAS_ERR_CUDA;
+    if (cudaMemcpyAsync(d_logits + (size_t)b0 * z->Z, z->logits, (size_t)B * z->Z * 4, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, float* d_logits,
+                       fdas_stream_t stream) {
+  if (!z || !d_spectrum || !d_logits || n_bins < 1 || n_bins > (int64_t(1) << 30)) return FDAS_ERR_INVALID;
+  const int hop = z->Wd / 2;
+  if (hop % 128 != 0 || hop > kMaxHop) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u))
+    return FDAS_ERR_ALIGN;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t nb = (n_bins + hop - 1) / hop;
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->partial, z->scale, st);
+  ProposeParams q;
+  q.spec = reinterpret_cast<const float2*>(d_spectrum);
+  q.n = n_bins;
+  q.scale = z->scale;
+  q.w = z->ph;
+  q.oW1 = z->lay.W1;
+  q.ob1 = z->lay.b1;
+  q.oW2 = z->lay.W2;
+  q.ob2 = z->lay.b2;
+  q.oW3 = z->lay.W3;
+  q.ob3 = z->lay.b3;
+  q.oWl = z->lay.Wl;
+  q.obl = z->lay.bl;
+  q.Z = z->Z;
+  q.hop = hop;
+  q.n_blocks = nb;
+  q.logits = d_logits;
+  q.status = z->status;
+  const unsigned grid = (unsigned)(nb < z->sm_count ? nb : z->sm_count);
+  propose_kernel<<<grid, 256, kProposeSmem, st>>>(q);
+  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_zband_check(fdas_zband* z, fdas_stream_t stream) {
+  if (!z) return FDAS_ERR_INVALID;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpy(&status, z->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (status != 0) {
+    cudaMemset(z->status, 0, 4);
+    return FDAS_ERR_TIMEOUT;
+  }
+  return FDAS_OK;
+}
+
+int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int window, int hop, float* d_windows,
+                                int64_t n_windows, fdas_stream_t stream) {
+  if (!d_spectrum || !d_windows || n_bins < 1 || n_bins > (int64_t(1) << 30) || window < 4 || window % 4 != 0 ||
+      window > (1 << 16) || hop < 1 || n_windows < 1 || n_windows > (1 << 30))
+    return FDAS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_spectrum) & 7u) return FDAS_ERR_ALIGN;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* partial = nullptr;
+  float* scale = nullptr;
+  if (cudaMallocAsync(&partial, kSumBlocks * sizeof(double), st) != cudaSuccess) return FDAS_ERR_ALLOC;
+  if (cudaMallocAsync(&scale, 4, st) != cudaSuccess) {
+    cudaFreeAsync(partial, st);
+    return FDAS_ERR_ALLOC;
+  }
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, partial, scale, st);
+  spectrum_windows_kernel<<<(unsigned)n_windows, 256, 0, st>>>(reinterpret_cast<const float2*>(d_spectrum), n_bins,
+                                                               scale, window, hop, d_windows);
+  const int rc = cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  cudaFreeAsync(partial, st);
+  cudaFreeAsync(scale, st);
+  return rc;
+}
+
+int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
+                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, int64_t* host_count,
+                          fdas_stream_t stream) {
+  if (!d_logits || !d_units || !host_count || n_windows < 1 || n_windows > (1 << 30) || Z < 1 ||
+      !(threshold > 0.f && threshold < 1.f) || hop < 1 || group_bins < 1 || h < 0 || n_groups < 1 ||
+      n_groups > (1 << 24) || (int64_t)n_groups * Z > INT32_MAX)
+    return FDAS_ERR_INVALID;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const float logit_thr = logf(threshold / (1.f - threshold));
+  unsigned char* flags = nullptr;
+  int* counts = nullptr;
+  int64_t* offsets = nullptr;
+  if (cudaMallocAsync(&flags, (size_t)n_groups * Z, st) != cudaSuccess) return FDAS_ERR_ALLOC;
+  if (cudaMallocAsync(&counts, (size_t)n_groups * 4, st) != cudaSuccess) {
+    cudaFreeAsync(flags, st);
+    return FDAS_ERR_ALLOC;
+  }
+  if (cudaMallocAsync(&offsets, (size_t)(n_groups + 1) * 8, st) != cudaSuccess) {
+    cudaFreeAsync(flags, st);
+    cudaFreeAsync(counts, st);
+    return FDAS_ERR_ALLOC;
+  }
+  group_flags_kernel<<<(unsigned)n_groups, 256, 0, st>>>(d_logits, (int)n_windows, Z, logit_thr, hop, group_bins, h,
+                                                        (int)n_groups, flags, counts);
+  scan_counts_kernel<<<1, 32, 0, st>>>(counts, (int)n_groups, offsets, offsets + n_groups);
+  write_units_kernel<<<(unsigned)n_groups, 32, 0, st>>>(flags, offsets, Z, d_units);
+  int rc = FDAS_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(host_count, offsets + n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    rc = FDAS_ERR_CUDA;
+  cudaFreeAsync(flags, st);
+  cudaFreeAsync(counts, st);
+  cudaFreeAsync(offsets, st);
+  return rc;
+}
+
+int fdas_zband_destroy(fdas_zband* z) {
+  if (!z) return FDAS_OK;
+  cudaDeviceSynchronize();
+  free_zband(z);
+  return FDAS_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfdas.so")
 
 FDAS_OK = 0
+FDAS_ERR_INVALID, FDAS_ERR_ALIGN, FDAS_ERR_NOT_BUILT, FDAS_ERR_ALLOC = -1, -2, -3, -4
+FDAS_ERR_CUDA, FDAS_ERR_NO_DEVICE, FDAS_ERR_UNSUPPORTED, FDAS_ERR_TIMEOUT = -5, -6, -7, -8
 ERRORS = {
     -1: "FDAS_ERR_INVALID", -2: "FDAS_ERR_ALIGN", -3: "FDAS_ERR_NOT_BUILT", -4: "FDAS_ERR_ALLOC",
     -5: "FDAS_ERR_CUDA", -6: "FDAS_ERR_NO_DEVICE", -7: "FDAS_ERR_UNSUPPORTED", -8: "FDAS_ERR_TIMEOUT",
@@ -27,7 +29,11 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_convolve_power_static", "fdas_selftest_wait_timeout",
             "fdas_batch_create", "fdas_batch_last_error", "fdas_batch_templates_build",
             "fdas_batch_convolve_power", "fdas_batch_check", "fdas_batch_destroy", "fdas_batch_info",
-            "fdas_batch_autotune"]
+            "fdas_batch_autotune", "fdas_plan_group_segments", "fdas_convolve_power_units",
+            "fdas_zband_create", "fdas_zband_param_count", "fdas_zband_set_params", "fdas_zband_get_params",
+            "fdas_zband_get_adam", "fdas_zband_set_adam", "fdas_zband_train_step", "fdas_zband_gradients",
+            "fdas_zband_predict", "fdas_zband_propose", "fdas_zband_check", "fdas_zband_spectrum_windows",
+            "fdas_zband_work_units", "fdas_zband_destroy"]
 
 _lock = threading.Lock()
 _lib = None
@@ -86,6 +92,39 @@ def lib() -> ctypes.CDLL:
             L.fdas_batch_info.restype = i32
             L.fdas_batch_autotune.argtypes = [i32, vp, vp, i32, i32, vp, i32, vp, vp, vp, vp, vp]
             L.fdas_batch_autotune.restype = i32
+            L.fdas_plan_group_segments.argtypes = [vp]
+            L.fdas_plan_group_segments.restype = i32
+            L.fdas_convolve_power_units.argtypes = [vp, vp, vp, vp, i64, vp]
+            L.fdas_convolve_power_units.restype = i32
+            f32 = ctypes.c_float
+            L.fdas_zband_create.argtypes = [i32, i32, i32]
+            L.fdas_zband_create.restype = vp
+            L.fdas_zband_param_count.argtypes = [vp]
+            L.fdas_zband_param_count.restype = i32
+            L.fdas_zband_set_params.argtypes = [vp, vp]
+            L.fdas_zband_set_params.restype = i32
+            L.fdas_zband_get_params.argtypes = [vp, vp]
+            L.fdas_zband_get_params.restype = i32
+            L.fdas_zband_get_adam.argtypes = [vp, vp, vp, vp]
+            L.fdas_zband_get_adam.restype = i32
+            L.fdas_zband_set_adam.argtypes = [vp, vp, vp, i32]
+            L.fdas_zband_set_adam.restype = i32
+            L.fdas_zband_propose.argtypes = [vp, vp, i64, vp, vp]
+            L.fdas_zband_propose.restype = i32
+            L.fdas_zband_check.argtypes = [vp, vp]
+            L.fdas_zband_check.restype = i32
+            L.fdas_zband_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp]
+            L.fdas_zband_train_step.restype = i32
+            L.fdas_zband_gradients.argtypes = [vp, vp]
+            L.fdas_zband_gradients.restype = i32
+            L.fdas_zband_predict.argtypes = [vp, vp, i32, i32, vp, vp]
+            L.fdas_zband_predict.restype = i32
+            L.fdas_zband_spectrum_windows.argtypes = [vp, i64, i32, i32, vp, i64, vp]
+            L.fdas_zband_spectrum_windows.restype = i32
+            L.fdas_zband_work_units.argtypes = [vp, i64, i32, f32, i32, i64, i32, i64, vp, vp, vp]
+            L.fdas_zband_work_units.restype = i32
+            L.fdas_zband_destroy.argtypes = [vp]
+            L.fdas_zband_destroy.restype = i32
             L.fdas_selftest_wait_timeout.argtypes = [vp, i64, vp]
             L.fdas_selftest_wait_timeout.restype = i32
             L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
@@ -161,6 +200,18 @@ class Plan:
     def check(self, stream=None):
         _check(lib().fdas_check(self._h, _stream(stream)), "fdas_check")
 
+    @property
+    def group_segments(self) -> int:
+        g = lib().fdas_plan_group_segments(self._h)
+        if g < 0:
+            raise FdasError(g, "fdas_plan_group_segments")
+        return g
+
+    def convolve_power_units(self, spectrum, plane, units, n_units: int, stream=None):
+        """Only the listed work units g*Z + z (ascending int32 device tensor) are computed."""
+        _check(lib().fdas_convolve_power_units(self._h, _ptr(spectrum), _ptr(plane), _ptr(units), int(n_units),
+                                               _stream(stream)), "fdas_convolve_power_units")
+
     def template_taps(self, z_idx: int) -> np.ndarray:
         out = np.empty(2 * (self.tmpl_len + 1), dtype=np.float64)
         _check(lib().fdas_template_taps(self._h, int(z_idx), out.ctypes.data), "fdas_template_taps")
@@ -187,6 +238,116 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class ZBand:
+    """fdas_zband: the z-band proposal network (training and inference kernels)."""
+
+    def __init__(self, window: int, n_out: int, max_batch: int):
+        h = lib().fdas_zband_create(int(window), int(n_out), int(max_batch))
+        if not h:
+            raise FdasError(-1, "fdas_zband_create")
+        self._h = h
+        self.window, self.n_out, self.max_batch = int(window), int(n_out), int(max_batch)
+        self.n_params = lib().fdas_zband_param_count(h)
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(lib().fdas_zband_set_params(self._h, p.ctypes.data), "fdas_zband_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().fdas_zband_get_params(self._h, out.ctypes.data), "fdas_zband_get_params")
+        return out
+
+    def gradients(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().fdas_zband_gradients(self._h, out.ctypes.data), "fdas_zband_gradients")
+        return out
+
+    def get_adam(self):
+        m = np.empty(self.n_params, dtype=np.float32)
+        v = np.empty(self.n_params, dtype=np.float32)
+        step = ctypes.c_int(0)
+        _check(lib().fdas_zband_get_adam(self._h, m.ctypes.data, v.ctypes.data, ctypes.byref(step)),
+               "fdas_zband_get_adam")
+        return m, v, step.value
+
+    def set_adam(self, m: np.ndarray, v: np.ndarray, step: int):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if m.size != self.n_params or v.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} moments")
+        _check(lib().fdas_zband_set_adam(self._h, m.ctypes.data, v.ctypes.data, int(step)), "fdas_zband_set_adam")
+
+    def save(self, path):
+        """Checkpoint: parameters, Adam moments and step count (numpy .npz)."""
+        m, v, step = self.get_adam()
+        np.savez(path, params=self.get_params(), m=m, v=v, step=np.int64(step),
+                 window=np.int64(self.window), n_out=np.int64(self.n_out))
+
+    def load(self, path):
+        with np.load(path) as f:
+            if int(f["window"]) != self.window or int(f["n_out"]) != self.n_out:
+                raise ValueError("checkpoint shape does not match this net")
+            self.set_params(f["params"])
+            self.set_adam(f["m"], f["v"], int(f["step"]))
+
+    def train_step(self, windows, targets, batch: int, lr: float, stream=None, want_loss: bool = True):
+        loss = ctypes.c_float(0.0)
+        _check(lib().fdas_zband_train_step(self._h, _ptr(windows), _ptr(targets), int(batch), float(lr),
+                                           ctypes.byref(loss) if want_loss else None, _stream(stream)),
+               "fdas_zband_train_step")
+        return loss.value if want_loss else None
+
+    def predict(self, windows, batch: int, logits, half_weights: bool = True, stream=None):
+        _check(lib().fdas_zband_predict(self._h, _ptr(windows), int(batch), 1 if half_weights else 0, _ptr(logits),
+                                        _stream(stream)), "fdas_zband_predict")
+
+    def n_blocks(self, n_bins: int) -> int:
+        hop = self.window // 2
+        return -(-int(n_bins) // hop)
+
+    def propose(self, spectrum, n_bins: int, logits, stream=None):
+        """Async: logits (n_blocks x Z float32) for every block of hop window/2 bins."""
+        _check(lib().fdas_zband_propose(self._h, _ptr(spectrum), int(n_bins), _ptr(logits), _stream(stream)),
+               "fdas_zband_propose")
+
+    def check(self, stream=None):
+        _check(lib().fdas_zband_check(self._h, _stream(stream)), "fdas_zband_check")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fdas_zband_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def zband_spectrum_windows(spectrum, n_bins: int, window: int, hop: int, windows, n_windows: int, stream=None):
+    _check(lib().fdas_zband_spectrum_windows(_ptr(spectrum), int(n_bins), int(window), int(hop), _ptr(windows),
+                                             int(n_windows), _stream(stream)), "fdas_zband_spectrum_windows")
+
+
+def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: int, group_bins: int, h: int,
+                     n_groups: int, units, stream=None) -> int:
+    count = ctypes.c_int64(0)
+    _check(lib().fdas_zband_work_units(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(hop),
+                                       int(group_bins), int(h), int(n_groups), _ptr(units), ctypes.byref(count),
+                                       _stream(stream)), "fdas_zband_work_units")
+    return count.value
 
 
 def _i64_array(values):

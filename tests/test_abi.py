@@ -110,3 +110,26 @@ def test_batch_create_validation_without_device(lib):
     assert lib.fdas_batch_check(None, None) == -1
     assert lib.fdas_batch_templates_build(None, None) == -1
     assert lib.fdas_batch_convolve_power(None, None, None, 0, None) == -1
+
+
+def test_null_and_invalid_zband_calls(lib):
+    """Host-side validation of the proposal network's calls (returns before any device work)."""
+    lib.fdas_zband_create.restype = ctypes.c_void_p
+    for args in [(100, 201, 8), (1000, 201, 8), (1 << 17, 201, 8), (1024, 0, 8), (1024, 70000, 8),
+                 (1024, 201, 0), (1024, 201, 70000)]:
+        assert not lib.fdas_zband_create(*args), args
+    assert lib.fdas_zband_param_count(None) == -1
+    assert lib.fdas_zband_set_params(None, None) == -1
+    assert lib.fdas_zband_get_params(None, None) == -1
+    assert lib.fdas_zband_get_adam(None, None, None, None) == -1
+    assert lib.fdas_zband_set_adam(None, None, None, 0) == -1
+    assert lib.fdas_zband_train_step(None, None, None, 1, 1e-3, None, None) == -1
+    assert lib.fdas_zband_gradients(None, None) == -1
+    assert lib.fdas_zband_predict(None, None, 1, 1, None, None) == -1
+    assert lib.fdas_zband_propose(None, None, 1024, None, None) == -1
+    assert lib.fdas_zband_check(None, None) == -1
+    assert lib.fdas_zband_spectrum_windows(None, 1024, 1024, 512, None, 3, None) == -1
+    assert lib.fdas_zband_work_units(None, 4, 201, ctypes.c_float(0.5), 512, 1536, 256, 2, None, None, None) == -1
+    assert lib.fdas_zband_destroy(None) == 0
+    assert lib.fdas_plan_group_segments(None) == -1
+    assert lib.fdas_convolve_power_units(None, None, None, None, 1, None) == -1

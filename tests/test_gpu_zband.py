@@ -1,0 +1,255 @@
+"""The learned z-band proposal on the GPU against the FP64 oracle (oracle/zband.py): windows of
+x, the windowed forward pass (FP32 and FP16 weights), gradients and the Adam step of training,
+the fused tensor-core inference over whole spectra, the work list, checkpoints, and the
+work-list correlation against the full plane."""
+import numpy as np
+import pytest
+
+from oracle import zband as oz
+from paper_1711_10855_gb300 import fdas, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NAMES = ["W1", "b1", "W2", "b2", "W3", "b3", "Wl", "bl"]
+
+
+def flat(params):
+    return np.concatenate([params[k].reshape(-1) for k in NAMES]).astype(np.float32)
+
+
+def unflat(vec, Z):
+    shapes = {"W1": (32, 1, 9), "b1": (32,), "W2": (32, 32, 9), "b2": (32,), "W3": (32, 32, 9), "b3": (32,),
+              "Wl": (Z, 32), "bl": (Z,)}
+    out, o = {}, 0
+    for k in NAMES:
+        n = int(np.prod(shapes[k]))
+        out[k] = np.asarray(vec[o:o + n], dtype=np.float64).reshape(shapes[k])
+        o += n
+    return out
+
+
+def make_params(Z, seed):
+    rng = np.random.default_rng(seed)
+    p = oz.init_params(Z, seed=seed, channels=32)
+    for k in ("b1", "b2", "b3", "bl"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.2
+    v = flat(p)
+    return v, unflat(v, Z)           # the FP32 vector and its exact FP64 values
+
+
+def chirp_spectrum(n_bins, seed, n_chirps=6, amp=0.08):
+    rng = np.random.default_rng(seed)
+    chirps = [synth.Chirp(float(rng.uniform(300, n_bins - 500)), float(rng.uniform(-150, 150)), amp,
+                          float(rng.uniform(0, 6.28))) for _ in range(n_chirps)]
+    return synth.spectrum_of(synth.time_series(2 * n_bins, chirps, seed))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_spectrum_windows_match_oracle():
+    n = 5000
+    spec = synth.noise_spectrum(n, 3)
+    spec[1234] *= 40.0                                 # a bin above the cap
+    W, H = 1024, 512
+    nw = oz.n_blocks(n, W)
+    d = torch.empty((nw, W), dtype=torch.float32, device="cuda")
+    fdas.zband_spectrum_windows(dev(spec), n, W, H, d, nw)
+    torch.cuda.synchronize()
+    want = oz.windows(oz.power_x(spec), W, H, nw)
+    got = d.cpu().numpy()
+    assert got.max() == np.float32(oz.X_CAP)
+    np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_windowed_forward_matches_oracle(half):
+    Z, W, B = 21, 256, 12
+    vec, p64 = make_params(Z, 11)
+    if half:
+        p64 = unflat(vec.astype(np.float16).astype(np.float32), Z)
+    spec = chirp_spectrum(4096, 12)
+    x = oz.windows(oz.power_x(spec), W, W // 2, B)
+    with fdas.ZBand(W, Z, 8) as net:                  # max_batch < B: predict runs in chunks
+        net.set_params(vec)
+        logits = torch.empty((B, Z), dtype=torch.float32, device="cuda")
+        net.predict(dev(x.astype(np.float32)), B, logits, half_weights=half)
+        torch.cuda.synchronize()
+        got = logits.cpu().numpy()
+    want = oz.forward(p64, x.astype(np.float32).astype(np.float64))
+    scale = max(1.0, np.abs(want).max())
+    np.testing.assert_allclose(got, want, rtol=0, atol=2e-5 * scale)
+
+
+def test_train_step_gradients_and_adam_match_oracle():
+    Z, W, B = 21, 256, 8
+    vec, p64 = make_params(Z, 21)
+    spec = chirp_spectrum(2048, 22)
+    x32 = oz.windows(oz.power_x(spec), W, W // 2, B).astype(np.float32)
+    rng = np.random.default_rng(23)
+    tgt = (rng.random((B, Z)) < 0.2).astype(np.float32)
+    loss_o, g_o = oz.loss_and_grads(p64, x32.astype(np.float64), tgt.astype(np.float64))
+    lr = 1e-3
+    with fdas.ZBand(W, Z, B) as net:
+        net.set_params(vec)
+        loss = net.train_step(dev(x32), dev(tgt), B, lr)
+        g = unflat(net.gradients(), Z)
+        p1 = net.get_params()
+        m, v, step = net.get_adam()
+    assert abs(loss - loss_o) <= 1e-5 * max(1.0, abs(loss_o))
+    for k in NAMES:
+        tol = 2e-3 * np.abs(g_o[k]).max() + 1e-9
+        np.testing.assert_allclose(g[k], g_o[k], rtol=0, atol=tol, err_msg=k)
+    gflat = flat(g).astype(np.float64)
+    want, m_o, v_o = oz.adam_step(vec.astype(np.float64), gflat, 0.0, 0.0, 1, lr)
+    assert step == 1
+    np.testing.assert_allclose(p1, want, rtol=0, atol=2e-7 + 1e-6 * lr)
+    np.testing.assert_allclose(m, m_o, rtol=1e-5, atol=1e-12)
+    # 1 - beta2 in FP32 (1 - 0.999f) is 1.3e-5 away from 0.001 in relative terms
+    np.testing.assert_allclose(v, v_o, rtol=3e-5, atol=1e-15)
+
+
+@pytest.mark.parametrize("W,n_bins", [(1024, 512 * 3 + 100), (1024, 40000), (512, 9000), (256, 3000)])
+def test_propose_matches_oracle_block_logits(W, n_bins):
+    """Fused tensor-core inference (FP16 weights and activations, FP32 accumulation) against the
+    FP64 windowed definition with the same FP16 weights; ragged last block included."""
+    Z = 21
+    vec, _ = make_params(Z, 31)
+    p16 = unflat(vec.astype(np.float16).astype(np.float32), Z)
+    spec = chirp_spectrum(n_bins, 32, n_chirps=max(1, n_bins // 6000), amp=0.2)
+    want = oz.block_logits(p16, spec, W)
+    with fdas.ZBand(W, Z, 4) as net:
+        net.set_params(vec)
+        nb = net.n_blocks(n_bins)
+        assert nb == want.shape[0]
+        logits = torch.full((nb, Z), float("nan"), dtype=torch.float32, device="cuda")
+        net.propose(dev(spec), n_bins, logits)
+        net.check()
+        got = logits.cpu().numpy()
+    scale = max(1.0, np.abs(want).max())
+    err = np.abs(got - want).max()
+    assert err <= 2e-2 * scale, (err, scale)
+
+
+def test_propose_large_spectrum_sampled_blocks_and_predict_agreement():
+    """2^20 bins (2048 blocks over the persistent grid): sampled blocks against the oracle, and
+    every block against the windowed CUDA-core path (same FP16 weights)."""
+    Z, W, n = 201, 1024, 1 << 20
+    vec, _ = make_params(Z, 41)
+    p16 = unflat(vec.astype(np.float16).astype(np.float32), Z)
+    spec = synth.spectrum(synth.Workload("zband-2^20", 2 * n, 200, 2, 512, 2048, 42,
+                                         tuple(synth.Chirp(float(r), float(z), 0.03, 0.0)
+                                               for r, z in [(1000, 150), (300000, -80), (1048000, 10)])))
+    with fdas.ZBand(W, Z, 256) as net:
+        net.set_params(vec)
+        nb = net.n_blocks(n)
+        logits = torch.empty((nb, Z), dtype=torch.float32, device="cuda")
+        d_spec = dev(spec)
+        net.propose(d_spec, n, logits)
+        net.check()
+        win = torch.empty((nb, W), dtype=torch.float32, device="cuda")
+        fdas.zband_spectrum_windows(d_spec, n, W, W // 2, win, nb)
+        ref = torch.empty((nb, Z), dtype=torch.float32, device="cuda")
+        net.predict(win, nb, ref, half_weights=True)
+        torch.cuda.synchronize()
+        got, alt = logits.cpu().numpy(), ref.cpu().numpy()
+        x = win.cpu().numpy()
+    sample = np.unique(np.r_[0, 1, 2, nb - 1, np.random.default_rng(43).integers(0, nb, 12), 585, 2046])
+    want = oz.forward(p16, x[sample].astype(np.float64))
+    scale = max(1.0, np.abs(want).max())
+    assert np.abs(got[sample] - want).max() <= 2e-2 * scale
+    assert np.abs(got - alt).max() <= 2e-2 * max(1.0, np.abs(alt).max())
+
+
+def test_work_units_match_oracle():
+    rng = np.random.default_rng(51)
+    nw, Z, thr = 37, 21, 0.3
+    logits = rng.normal(-2.0, 2.0, (nw, Z)).astype(np.float32)
+    lthr = np.log(thr / (1 - thr))
+    near = np.abs(logits - lthr) < 1e-3
+    logits[near] += 0.01
+    hop, V, G, h = 512, 1536, 8, 256
+    n_groups = 2
+    units = torch.empty(n_groups * Z, dtype=torch.int32, device="cuda")
+    n = fdas.zband_work_units(dev(logits), nw, Z, thr, hop, G * V, h, n_groups, units)
+    want = oz.work_units(logits.astype(np.float64), thr, hop, G * V, h, n_groups)
+    assert n == want.size
+    np.testing.assert_array_equal(units[:n].cpu().numpy(), want)
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    Z, W, B = 21, 256, 4
+    vec, _ = make_params(Z, 61)
+    spec = chirp_spectrum(2048, 62)
+    x = dev(oz.windows(oz.power_x(spec), W, W // 2, B).astype(np.float32))
+    y = dev((np.random.default_rng(63).random((B, Z)) < 0.3).astype(np.float32))
+    with fdas.ZBand(W, Z, B) as a, fdas.ZBand(W, Z, B) as b:
+        a.set_params(vec)
+        for _ in range(3):
+            a.train_step(x, y, B, 1e-3)
+        path = tmp_path / "zband.npz"
+        a.save(path)
+        b.load(path)
+        np.testing.assert_array_equal(a.get_params(), b.get_params())
+        ma, va, sa = a.get_adam()
+        mb, vb, sb = b.get_adam()
+        assert sa == sb == 3
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+        a.train_step(x, y, B, 1e-3)
+        b.train_step(x, y, B, 1e-3)
+        np.testing.assert_allclose(a.get_params(), b.get_params(), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("L,m,n_bins", [(2048, 512, 200_000), (512, 64, 70_004)])
+def test_convolve_power_units_cells_equal_the_full_plane(L, m, n_bins):
+    zmax, zstep = 20, 2
+    spec = dev(synth.noise_spectrum(n_bins, 71))
+    with fdas.Plan(n_bins, zmax, zstep, L, m) as plan:
+        plan.build_templates()
+        Z = plan.n_z
+        full = torch.empty((Z, n_bins), dtype=torch.float32, device="cuda")
+        plan.convolve_power(spec, full)
+        plan.check()
+        G = plan.group_segments
+        n_groups = -(-plan.n_seg // G)
+        rng = np.random.default_rng(72)
+        keep = rng.random(n_groups * Z) < 0.3
+        keep[-1] = keep[0] = True
+        keep[Z:2 * Z] = True                        # one whole group
+        units = np.flatnonzero(keep).astype(np.int32)
+        part = torch.full((Z, n_bins), float("nan"), dtype=torch.float32, device="cuda")
+        plan.convolve_power_units(spec, part, dev(units), units.size)
+        plan.check()
+        f, p = full.cpu().numpy(), part.cpu().numpy()
+    mask = np.zeros((Z, n_bins), dtype=bool)
+    gb = G * plan.valid
+    for u in units:
+        g, z = divmod(int(u), Z)
+        mask[z, g * gb:(g + 1) * gb] = True
+    np.testing.assert_array_equal(p[mask], f[mask])
+    assert np.all(np.isnan(p[~mask]))
+
+
+def test_convolve_power_units_rejects_bad_lists_on_the_device():
+    n_bins, L, m = 50_000, 2048, 512
+    spec = dev(synth.noise_spectrum(n_bins, 81))
+    with fdas.Plan(n_bins, 10, 2, L, m) as plan:
+        plan.build_templates()
+        Z = plan.n_z
+        n_groups = -(-plan.n_seg // plan.group_segments)
+        part = torch.full((Z, n_bins), float("nan"), dtype=torch.float32, device="cuda")
+        for bad in ([0, 5, 3], [1, 2, n_groups * Z], [-1, 0, 1], [4, 4]):
+            plan.convolve_power_units(spec, part, dev(np.asarray(bad, dtype=np.int32)), len(bad))
+            with pytest.raises(fdas.FdasError) as e:
+                plan.check()
+            assert e.value.code == fdas.FDAS_ERR_INVALID
+        assert torch.isnan(part).all()
+        good = dev(np.asarray([0, Z + 3], dtype=np.int32))
+        plan.convolve_power_units(spec, part, good, 2)
+        plan.check()
+        assert not torch.isnan(part[0, :10]).any()
+        with pytest.raises(fdas.FdasError):
+            plan.convolve_power_units(spec, part, good, 0)
