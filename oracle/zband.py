@@ -5,7 +5,8 @@ template is a unit impulse, so Eq. 2 gives P[0][r] = |A_r|^2) and predicts which
 the z grid are worth correlating near each block of bins.  The paper has no such network; this
 is the plain definition the CUDA kernels are checked against.
 
-    x_r    = min(|A_r|^2 / mean_r' |A_r'|^2, X_CAP)       whole-spectrum mean, cap 64
+    x_r    = min(|A_r|^2 * ln 2 / med, X_CAP)     med = lower median of |A_r'|^2 over the
+                                                   whole spectrum (noise: E x = 1), cap 64
     window w (width W, hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
     h1     = relu(conv_k9(x;  W1 (32,1,9),  b1))        zero padding 4 ("same") at the window edge
     h2     = relu(conv_k9(h1; W2 (32,32,9), b2))
@@ -60,11 +61,13 @@ X_CAP = 64.0
 
 
 def power_x(spectrum: np.ndarray) -> np.ndarray:
-    """x_r = min(|A_r|^2 / mean |A|^2, X_CAP) in FP64 (spectrum: complex n-vector)."""
+    """x_r = min(|A_r|^2 * ln 2 / med, X_CAP), med the lower median (rank (n-1)//2) of |A|^2.
+    For white noise |A_r|^2 is exponential, whose median is ln 2 times its mean, so noise bins
+    have E x = 1 however many bins carry signal (up to half).  A zero median gives x = 0."""
     a = np.asarray(spectrum).astype(np.complex128)
     p = a.real ** 2 + a.imag ** 2
-    mean = p.mean()
-    x = p / mean if mean > 0 else np.zeros_like(p)
+    med = np.partition(p, (p.size - 1) // 2)[(p.size - 1) // 2]
+    x = p * (np.log(2.0) / med) if med > 0 else np.zeros_like(p)
     return np.minimum(x, X_CAP)
 
 

@@ -60,14 +60,37 @@ def test_pooling_window_is_the_centre_half():
 
 
 def test_power_x_closed_form_and_cap():
-    a = np.array([1.0, 1j, 2.0, 0.0])
-    np.testing.assert_allclose(zband.power_x(a), [2 / 3, 2 / 3, 8 / 3, 0.0], rtol=1e-15)
-    b = np.ones(1000, dtype=complex)
-    b[7] = 100.0                       # |A|^2 = 1e4, mean ~ 10.99 -> x ~ 910 -> capped
-    x = zband.power_x(b)
+    ln2 = np.log(2.0)
+    a = np.array([1.0, 1j, 2.0, 0.0])            # |A|^2 = 1, 1, 4, 0: lower median 1
+    np.testing.assert_allclose(oz_px(a), [ln2, ln2, 4 * ln2, 0.0], rtol=1e-15)
+    b = np.array([3.0, 1.0, 2.0])                # |A|^2 = 9, 1, 4: median 4
+    np.testing.assert_allclose(oz_px(b), [9 * ln2 / 4, ln2 / 4, ln2], rtol=1e-15)
+    c = np.ones(1001, dtype=complex)
+    c[7] = 100.0                                 # 1e4 * ln 2 -> capped; the median ignores it
+    x = oz_px(c)
     assert x[7] == zband.X_CAP
-    np.testing.assert_allclose(x[0], 1000.0 / (999.0 + 1e4), rtol=1e-15)
-    assert np.all(zband.power_x(np.zeros(8)) == 0.0)
+    np.testing.assert_allclose(x[0], ln2, rtol=1e-15)
+    assert np.all(oz_px(np.zeros(8)) == 0.0)
+    d = np.zeros(9, dtype=complex)
+    d[:4] = 5.0                                  # more than half zero: median 0 -> x = 0
+    assert np.all(oz_px(d) == 0.0)
+
+
+def test_power_x_noise_has_unit_mean_despite_signals():
+    """Exponential noise: median = ln 2 * mean, so x has mean 1; strong signals in 20% of the
+    bins barely move the median (they would move a mean by orders of magnitude)."""
+    rng = np.random.default_rng(8)
+    n = 200_000
+    a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / np.sqrt(2.0)
+    x = oz_px(a)
+    assert abs(x.mean() - 1.0) < 0.01
+    a[: n // 5] *= 30.0
+    x = oz_px(a)
+    assert abs(np.median(x[n // 5:]) / np.log(2.0) - 1.0) < 0.35
+
+
+def oz_px(a):
+    return zband.power_x(a)
 
 
 def test_windows_by_index_and_centre_halves_tile_the_spectrum():
