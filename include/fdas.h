@@ -224,7 +224,8 @@ int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d
  * z = 0 power spectrum (the plane's z = 0 row, Eq. 2 with the unit-impulse template) that
  * predicts, for each block of bins, which of Z templates are worth correlating there.
  *
- *   x_r    = min(|A_r|^2 / mean_r' |A_r'|^2, 64)   one scale for the whole spectrum
+ *   x_r    = min(|A_r|^2 * ln 2 / med, 64)   med: lower median (rank (n-1)/2) of |A|^2 over the
+ *            whole spectrum, so white-noise bins have mean 1 whatever the signals (x = 0 if med = 0)
  *   window w of width W (hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
  *   three k = 9 convolutions, 32 channels, zero padding 4 at the window edge, ReLU;
  *   the maximum of each channel over the central half [W/4, 3W/4) (= block [w*H, (w+1)*H));
@@ -233,7 +234,8 @@ int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d
  * Parameters are one FP32 vector: W1 [32][1][9], b1 [32], W2 [32][32][9], b2 [32],
  * W3 [32][32][9], b3 [32], Wl [Z][32], bl [Z]; an FP16 copy is kept for inference.
  * Training (FP32 forward, backward and Adam) and windowed inference run on the CUDA cores;
- * fdas_zband_propose runs the layers once over a whole spectrum on the tensor cores.
+ * fdas_zband_propose runs the layers once over a whole spectrum on the tensor cores.  The median
+ * is found exactly on the device (radix selection on the FP32 bit patterns of |A_r|^2).
  * ------------------------------------------------------------------------------------------- */
 typedef struct fdas_zband fdas_zband;
 

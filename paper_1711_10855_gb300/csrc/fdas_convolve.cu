@@ -416,7 +416,7 @@ __device__ __forceinline__ SpecDesc spectrum_desc(const BatchParams& p, int b) {
 // takes a contiguous equal range.  Segment s of spectrum b is brought in by one bulk copy of its
 // part inside [0, n_b) (cp.async.bulk) and the rest of the L-bin window is zero-filled by the
 // owning warp.
-template <class Cfg, int NV>
+template <class Cfg, int NV, bool LIST>
 __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchParams p) {
   constexpr int L = Cfg::L, N1 = Cfg::N1, R = Cfg::R, G = Cfg::G, H2 = Cfg::H2, W = Cfg::W;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -444,13 +444,18 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
 
   const int64_t U = p.units;
   // flattened unit of list entry e (identity without a work list)
-  auto unit_at = [&](int64_t e) -> int64_t { return p.unit_list ? (int64_t)__ldg(p.unit_list + e) : e; };
+  auto unit_at = [&](int64_t e) -> int64_t {
+    if constexpr (LIST) return (int64_t)__ldg(p.unit_list + e);
+    else return e;
+  };
   const int64_t u0 = (int64_t)blockIdx.x * U / gridDim.x;
   const int64_t u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
   const int64_t npos = u1 - u0;
   if (npos <= 0) return;
   // a work list that failed its check (status bit 2, set by the preceding check kernel) is not run
-  if (p.unit_list && (*reinterpret_cast<volatile const int*>(p.status) & 2)) return;
+  if constexpr (LIST) {
+    if (*reinterpret_cast<volatile const int*>(p.status) & 2) return;
+  }
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) {
@@ -479,10 +484,12 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   auto issue_template = [&](int64_t i) {
     const int slot = (int)(i % R);
     issued_pos[slot] = i;
-    const int64_t zrow = p.unit_list ? cur->z_off + unit_at(u0 + i) % cur->Z : cur->z_off + cur->z;
+    int64_t zrow;
+    if constexpr (LIST) zrow = cur->z_off + unit_at(u0 + i) % cur->Z;
+    else zrow = cur->z_off + cur->z;
     mbar_arrive_expect_tx(&full[slot], L * 8);
     bulk_g2s(sT + (size_t)slot * L, p.templates + (size_t)zrow * L, L * 8, &full[slot]);
-    if (p.unit_list) return;   // single spectrum: the cursor's spectrum never changes
+    if constexpr (LIST) return;   // single spectrum: the cursor's spectrum never changes
     cur->u += 1;
     cur->z = cur->z + 1 == cur->Z ? 0 : cur->z + 1;
     if (cur->u == cur->spec_end && cur->u < U) {
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     const int64_t grp = (uu - d.unit_base) / d.Z;
     const int64_t z_first = (uu - d.unit_base) % d.Z;
     int64_t grp_end;
-    if (p.unit_list) {
+    if constexpr (LIST) {
       grp_end = u + 1;
       while (grp_end < u1 && unit_at(grp_end) / d.Z == grp) ++grp_end;
     } else {
@@ -615,7 +622,9 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
         break;
       }
       // row of this position: consecutive templates without a list, the entry's own with one
-      const int64_t z = p.unit_list ? unit_at(u0 + i) % d.Z : z_first + (int64_t)(i - a);
+      int64_t z;
+      if constexpr (LIST) z = unit_at(u0 + i) % d.Z;
+      else z = z_first + (int64_t)(i - a);
       const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
 
       // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
@@ -771,7 +780,8 @@ using Cfg2048 = ConvCfg<2048, 32, 4, 1, 2>;
 
 template <class Cfg, int NV>
 static cudaError_t launch_tmem_nv(const BatchParams& p, int sm_count, cudaStream_t st) {
-  auto kern = fdas_convolve_tmem_kernel<Cfg, NV>;
+  // the work-list variant is a separate instantiation: the full-plane code stays free of it
+  auto kern = p.unit_list ? fdas_convolve_tmem_kernel<Cfg, NV, true> : fdas_convolve_tmem_kernel<Cfg, NV, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
   const int64_t grid = p.units < sm_count ? p.units : sm_count;

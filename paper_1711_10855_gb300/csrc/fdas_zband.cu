@@ -7,7 +7,7 @@
 // recall is measured.
 //
 // Network (window width Wd, hop Wd/2, C = 32 channels, k = 9, zero padding 4):
-//   x_r = min(|A_r|^2 / mean |A|^2, 64)   (one scale for the whole spectrum)
+//   x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)   (one scale for the whole spectrum)
 //   window w = x over bins [w*hop - Wd/4, w*hop + 3Wd/4), 0 outside [0, n)
 //   a1 = conv(x; W1, b1), a2 = conv(relu(a1); W2, b2), a3 = conv(relu(a2); W3, b3)
 //   m[c] = max over t in [Wd/4, 3Wd/4) of relu(a3[c][t]),   logits = Wl m + bl  (Z outputs)
@@ -23,8 +23,8 @@
 #include <cuda_runtime.h>
 
 #include "fdas.h"
-#include "fdas_device.cuh"
 #include "fdas_internal.h"
+#include "fdas_umma.cuh"
 
 namespace {
 
@@ -49,45 +49,75 @@ struct Layout {
   }
 };
 
-constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 / mean |A|^2, 64)
-constexpr int kSumBlocks = 512;  // fixed grid of the power reduction (deterministic order)
+constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)
+constexpr int kSelBlocks = 1024; // grid of the median passes
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
-// Whole-spectrum power sum in a fixed order: block b sums bins b*256 + t + k*512*256 in double
-// and writes partial[b]; power_scale_kernel folds the partials into scale = n / sum.
-__global__ void __launch_bounds__(256) power_partial_kernel(const float2* spec, int64_t n, double* partial) {
-  __shared__ double red[256];
-  double s = 0.0;
-  for (int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x; r < n; r += (int64_t)kSumBlocks * 256) {
-    const float2 a = spec[r];
-    s += (double)fmaf(a.x, a.x, a.y * a.y);
-  }
-  red[threadIdx.x] = s;
+// Exact lower median of |A_r|^2 (rank (n-1)/2) by radix selection on the FP32 bit patterns
+// (non-negative floats order as unsigned integers): four passes of 8 bits, most significant
+// first.  Each pass histograms the digit of the values whose higher bits equal the prefix
+// found so far; select_pick_kernel then fixes that digit.  scale = ln 2 / median.
+struct SelectState {
+  unsigned prefix, mask;   // bits fixed so far and their mask
+  long long k;             // rank of the median among the values matching the prefix
+  unsigned hist[256];
+};
+
+__device__ __forceinline__ float power_of(const float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+__global__ void __launch_bounds__(256) select_hist_kernel(const float2* spec, int64_t n, SelectState* st, int shift) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0u;
   __syncthreads();
-  for (int k = 128; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
+  const unsigned prefix = st->prefix, mask = st->mask;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
+    const int64_t r = base + threadIdx.x;
+    unsigned bucket = 256u;
+    if (r < n) {
+      const unsigned bits = __float_as_uint(power_of(__ldg(spec + r)));
+      if ((bits & mask) == prefix) bucket = (bits >> shift) & 255u;
+    }
+    // one shared atomic per distinct bucket of the warp
+    const unsigned peers = __match_any_sync(0xffffffffu, bucket);
+    if (bucket < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[bucket], (unsigned)__popc(peers));
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
 }
 
-__global__ void __launch_bounds__(kSumBlocks) power_scale_kernel(const double* partial, int64_t n, float* scale) {
-  __shared__ double red[kSumBlocks];
-  red[threadIdx.x] = partial[threadIdx.x];
-  __syncthreads();
-  for (int k = kSumBlocks / 2; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
+__global__ void select_pick_kernel(SelectState* st, int shift, float* scale) {
+  if (threadIdx.x != 0) return;
+  long long k = st->k;
+  int d = 0;
+  for (; d < 255; ++d) {
+    if (k < (long long)st->hist[d]) break;
+    k -= st->hist[d];
   }
-  if (threadIdx.x == 0) *scale = red[0] > 0.0 ? (float)((double)n / red[0]) : 0.f;
+  st->prefix |= (unsigned)d << shift;
+  st->mask |= 255u << shift;
+  st->k = k;
+  for (int i = 0; i < 256; ++i) st->hist[i] = 0u;
+  if (shift == 0) {
+    const float med = __uint_as_float(st->prefix);
+    *scale = med > 0.f ? 0.69314718055994531f / med : 0.f;
+  }
+}
+
+__global__ void select_init_kernel(SelectState* st, int64_t n) {
+  if (threadIdx.x == 0) {
+    st->prefix = 0u;
+    st->mask = 0u;
+    st->k = (n - 1) / 2;
+  }
+  st->hist[threadIdx.x] = 0u;
 }
 
 __device__ __forceinline__ float power_x(const float2* spec, int64_t n, int64_t r, float scale) {
   if (r < 0 || r >= n) return 0.f;
-  const float2 a = spec[r];
-  return fminf(fmaf(a.x, a.x, a.y * a.y) * scale, kXCap);
+  return fminf(power_of(spec[r]) * scale, kXCap);
 }
 
 // Windows of x: window w covers bins [w*hop - Wd/4, w*hop + 3Wd/4), 0 outside [0, n).
@@ -352,13 +382,15 @@ __global__ void write_units_kernel(const unsigned char* flags, const int64_t* of
 
 // ---------------------------------------------------------------------------------------
 // Fused inference over a whole spectrum on the tensor cores (tcgen05.mma kind::f16: FP16
-// weights and activations, FP32 accumulation in TMEM).  One CTA per SM walks blocks
-// w = blockIdx.x, blockIdx.x + gridDim.x, ...; block w owns output positions [w*hop, (w+1)*hop)
-// and recomputes the +-12-position halo its three layers need:
-//   x   at positions P0-12 .. (staged in shared memory, FP32)
-//   h1  at P0-8 + r, r < 128*T2 + 8      (layer 1 as an im2col GEMM: K = 9 taps padded to 16)
-//   h2  at P0-4 + r, r < hop + 8         (layer 2: T2 M-tiles of 128 positions)
-//   h3  at P0 + r,   r < hop             (layer 3: T3 = hop/128 M-tiles), max-pooled per channel
+// weights and activations, FP32 accumulation in TMEM).  A CTA holds the weights once and runs
+// two independent groups of 4 warps, each with its own activation slot, half of the TMEM
+// allocation, mbarrier and named barriers, so one group's MMAs overlap the other's epilogues.
+// Group g of CTA b walks blocks w = 2b + g, 2b + g + 2*gridDim.x, ...; block w owns output
+// positions [w*hop, (w+1)*hop) and recomputes the +-12-position halo its three layers need:
+//   x   at P0-12 + j, j < 128*T1 + 8     (prefetched into registers one block ahead)
+//   h1  at P0-8 + r,  r < 128*T2 + 8     (layer 1 as an im2col GEMM: K = 9 taps padded to 16)
+//   h2  at P0-4 + r,  r < hop + 8        (layer 2: T2 M-tiles of 128 positions)
+//   h3  at P0 + r,    r < hop            (layer 3: T3 = hop/128 M-tiles), max-pooled per channel
 // Activations sit in shared memory "chunk-planar": channel chunk j (8 channels, 16 B) of
 // position row r at plane j, offset 16*r.  A K-major no-swizzle operand whose rows are
 // positions is then one descriptor per (tap k, K-half c): start row + k, LBO = plane size,
@@ -372,25 +404,36 @@ constexpr int kNP1 = 128 * kT2max + 8;          // h1 rows (plane height)
 constexpr int kNP2 = 128 * kT2max;              // h2 rows (plane height)
 constexpr int kNA1 = 128 * kT1max;              // im2col rows of layer 1
 constexpr int kNX = kNA1 + 8;                   // staged x values
+constexpr int kGroupThreads = 128;
+constexpr int kXPer = (kNX + kGroupThreads - 1) / kGroupThreads;   // prefetched x per thread
+constexpr int kZStage = 256;                    // head weights staged in shared memory up to this Z
 constexpr uint32_t kPlaneH1 = kNP1 * 16, kPlaneH2 = kNP2 * 16, kPlaneA1 = kNA1 * 16;
 constexpr int kOffW1 = 0;                       // layer-1 weights: 2 K-chunks x 512 B
 constexpr int kOffW2 = kOffW1 + 1024;           // 9 taps x 4 K-chunks x 512 B
 constexpr int kOffW3 = kOffW2 + 9 * 2048;
-constexpr int kOffH1 = kOffW3 + 9 * 2048;       // also holds the staged x (dead before h1 is written)
-constexpr int kOffH2 = kOffH1 + 4 * kPlaneH1;   // also holds the layer-1 im2col (dead before h2)
-constexpr int kOffMisc = kOffH2 + 4 * kPlaneH2;
-constexpr int kProposeSmem = kOffMisc + 3 * kC * 4 + kC * 4 + 16 + 16;
+constexpr int kOffWl = kOffW3 + 9 * 2048;       // head weights [Z][32] FP16
+constexpr int kOffBl = kOffWl + kZStage * kC * 2;
+constexpr int kOffBias = kOffBl + kZStage * 4;  // b1, b2, b3 (FP32 values of the FP16 copy)
+constexpr int kOffSlot = kOffBias + 3 * kC * 4; // two activation slots
+constexpr int kSlotH1 = 0;                      // also holds the staged x (dead before h1 is written)
+constexpr int kSlotH2 = 4 * kPlaneH1;           // also holds the layer-1 im2col (dead before h2)
+constexpr int kSlotBytes = kSlotH2 + 4 * kPlaneH2;
+constexpr int kOffGroup = kOffSlot + 2 * kSlotBytes;   // per group: channel maxima, mbarrier
+constexpr int kGroupMisc = 256;
+constexpr int kOffTslot = kOffGroup + 2 * kGroupMisc;
+constexpr int kProposeSmem = kOffTslot + 16;
 constexpr uint32_t kIdesc = fdas::umma_idesc_f16(128, kC);
-constexpr uint32_t kTmemCols = 256;             // one layer's accumulators at a time (<= 6 x 32 columns)
+constexpr uint32_t kTmemCols = 512;             // 256 columns per group (<= 6 x 32 used)
 static_assert(2 * kPlaneA1 <= 4 * kPlaneH2, "im2col must fit in the h2 planes");
 static_assert(kNX * 4 <= (int)(4 * kPlaneH1), "staged x must fit in the h1 planes");
-static_assert(32 * kT1max <= (int)kTmemCols, "accumulators must fit the TMEM allocation");
+static_assert(32 * kT1max <= (int)kTmemCols / 2, "accumulators must fit a group's TMEM half");
+static_assert(kOffSlot % 128 == 0 && kSlotBytes % 128 == 0, "slot alignment");
 static_assert(kProposeSmem <= 227 * 1024, "shared memory");
 
 struct ProposeParams {
   const float2* spec;
   int64_t n;
-  const float* scale;       // n / sum |A|^2 (device scalar)
+  const float* scale;       // ln 2 / median |A|^2 (device scalar)
   const __half* w;          // FP16 parameter vector (Layout order)
   int oW1, ob1, oW2, ob2, oW3, ob3, oWl, obl;
   int Z, hop;
@@ -402,23 +445,42 @@ struct ProposeParams {
 // B operand (weights) of one tap in the K-major no-swizzle layout: rows o (N = 32), K = in-ch.
 __device__ __forceinline__ int wb_off(int o, int i) { return (i >> 3) * 512 + (o >> 3) * 128 + (o & 7) * 16 + (i & 7) * 2; }
 
+// Named barrier of one 128-thread group (ids 1, 2; id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
+__device__ __forceinline__ int group_all(int g, int v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(v), "r"(g + 1)
+      : "memory");
+  return r;
+}
+
 __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) {
   using namespace fdas;
   extern __shared__ __align__(1024) unsigned char sm[];
   __half* sW1 = reinterpret_cast<__half*>(sm + kOffW1);
   __half* sW2 = reinterpret_cast<__half*>(sm + kOffW2);
   __half* sW3 = reinterpret_cast<__half*>(sm + kOffW3);
-  float* sX = reinterpret_cast<float*>(sm + kOffH1);
-  unsigned char* sH1 = sm + kOffH1;
-  unsigned char* sH2 = sm + kOffH2;
-  unsigned char* sA1 = sm + kOffH2;
-  float* sBias = reinterpret_cast<float*>(sm + kOffMisc);            // b1, b2, b3
-  unsigned* sMax = reinterpret_cast<unsigned*>(sBias + 3 * kC);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sMax + kC);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  __half* sWl = reinterpret_cast<__half*>(sm + kOffWl);
+  float* sBl = reinterpret_cast<float*>(sm + kOffBl);
+  float* sBias = reinterpret_cast<float*>(sm + kOffBias);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffTslot);
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, half = warp >> 2;
-  // weights into the B layouts (FP16), biases as FP32 values of the FP16 copy
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 2, q = warp & 3, gt = tid & (kGroupThreads - 1);
+  unsigned char* slot = sm + kOffSlot + g * kSlotBytes;
+  float* sX = reinterpret_cast<float*>(slot + kSlotH1);
+  unsigned char* sH1 = slot + kSlotH1;
+  unsigned char* sH2 = slot + kSlotH2;
+  unsigned char* sA1 = slot + kSlotH2;
+  unsigned* sMax = reinterpret_cast<unsigned*>(sm + kOffGroup + g * kGroupMisc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffGroup + g * kGroupMisc + 128);
+  const bool wl_staged = p.Z <= kZStage;
+
+  // weights into the B layouts (FP16) and the head; biases as FP32 values of the FP16 copy
   for (int idx = tid; idx < kC * 16; idx += 256) {
     const int o = idx >> 4, k = idx & 15;
     sW1[wb_off(o, k) / 2] = k < kK ? p.w[p.oW1 + o * kK + k] : __float2half_rn(0.f);
@@ -428,12 +490,16 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     sW2[k * 1024 + wb_off(o, i) / 2] = p.w[p.oW2 + (o * kC + i) * kK + k];
     sW3[k * 1024 + wb_off(o, i) / 2] = p.w[p.oW3 + (o * kC + i) * kK + k];
   }
+  if (wl_staged) {
+    for (int idx = tid; idx < p.Z * kC; idx += 256) sWl[idx] = p.w[p.oWl + idx];
+    for (int j = tid; j < p.Z; j += 256) sBl[j] = __half2float(p.w[p.obl + j]);
+  }
   if (tid < kC) {
     sBias[tid] = __half2float(p.w[p.ob1 + tid]);
     sBias[kC + tid] = __half2float(p.w[p.ob2 + tid]);
     sBias[2 * kC + tid] = __half2float(p.w[p.ob3 + tid]);
   }
-  if (tid == 0) {
+  if (gt == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
@@ -445,25 +511,42 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  const uint32_t tm = *tslot;
+  const uint32_t tm = *tslot + 256u * g;
   const uint32_t tm_lane = tm + ((uint32_t)(32 * q) << 16);
   const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
   const uint32_t aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aA1 = smem_u32(sA1);
   const float sc = *p.scale;
   const int T3 = p.hop / 128, T2 = T3 + 1, T1 = T2 + 1;
+  const int nx = 128 * T1 + 8;
   uint32_t phase = 0;
   bool ok = true;
 
-  // wait for the MMAs committed last; every thread, bounded
+  // x values of block w's staging window into registers (all loads issued before any use)
+  float2 xa[kXPer];
+  auto load_x = [&](int64_t P0) {
+#pragma unroll
+    for (int e = 0; e < kXPer; ++e) {
+      const int j = gt + kGroupThreads * e;
+      const int64_t r = P0 - 12 + j;
+      xa[e] = (j < nx && r >= 0 && r < p.n) ? __ldg(p.spec + r) : make_float2(0.f, 0.f);
+    }
+  };
+  // wait for this group's committed MMAs; every thread of the group, bounded
   auto wait_mma = [&]() -> bool {
-    const int good = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0);
+    const int good = group_all(g, mbar_wait(bar, phase) ? 1 : 0);
     phase ^= 1u;
     tmem_fence_after_sync();
     return good != 0;
   };
+  auto sync_for_mma = [&]() {
+    fence_proxy_async_smem();
+    tmem_fence_before_sync();
+    group_sync(g);
+    tmem_fence_after_sync();
+  };
   // accumulator tile t (lanes = rows 128t + 32q + lane) + bias -> relu -> FP16 planes, rows < limit
   auto store_layer = [&](int ntiles, int limit, const float* bias, unsigned char* dst, uint32_t plane) {
-    for (int t = half; t < ntiles; t += 2) {
+    for (int t = 0; t < ntiles; ++t) {
       float a[16], b[16];
       tmem_ld16(tm_lane + 32 * t, a);
       tmem_ld16(tm_lane + 32 * t + 16, b);
@@ -484,23 +567,33 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       }
     }
   };
-  // one k = 9 convolution layer: ntiles M-tiles, A rows start at 128t + k in the source planes
+  // one k = 9 convolution layer: ntiles M-tiles, A rows start at 128t + k in the source planes;
+  // tiles innermost, so consecutive MMAs feed independent accumulators
   auto issue_conv = [&](int ntiles, uint32_t src, uint32_t plane, uint32_t wts) {
-    for (int t = 0; t < ntiles; ++t)
-      for (int k = 0; k < kK; ++k)
-        for (int c = 0; c < 2; ++c)
-          umma_f16(tm + 32 * t, umma_desc(src + (uint32_t)(128 * t + k) * 16 + 2 * c * plane, plane, 128),
-                   umma_desc(wts + k * 2048 + c * 1024, 512, 128), kIdesc, (k | c) != 0);
+    for (int k = 0; k < kK; ++k)
+      for (int c = 0; c < 2; ++c) {
+        const uint64_t bd = umma_desc(wts + k * 2048 + c * 1024, 512, 128);
+        for (int t = 0; t < ntiles; ++t)
+          umma_f16(tm + 32 * t, umma_desc(src + (uint32_t)(128 * t + k) * 16 + 2 * c * plane, plane, 128), bd,
+                   kIdesc, (k | c) != 0);
+      }
     umma_commit(bar);
   };
 
-  for (int64_t w = blockIdx.x; w < p.n_blocks; w += gridDim.x) {
-    const int64_t P0 = w * p.hop;
-    for (int j = tid; j < 128 * T1 + 8; j += 256) sX[j] = power_x(p.spec, p.n, P0 - 12 + j, sc);
-    if (tid < kC) sMax[tid] = 0u;
-    __syncthreads();
+  const int64_t wstep = 2 * (int64_t)gridDim.x;
+  int64_t w = 2 * (int64_t)blockIdx.x + g;
+  if (w < p.n_blocks) load_x(w * p.hop);
+  for (; w < p.n_blocks; w += wstep) {
+#pragma unroll
+    for (int e = 0; e < kXPer; ++e) {
+      const int j = gt + kGroupThreads * e;
+      if (j < nx) sX[j] = fminf(power_of(xa[e]) * sc, kXCap);
+    }
+    if (gt < kC) sMax[gt] = 0u;
+    group_sync(g);
+    if (w + wstep < p.n_blocks) load_x((w + wstep) * p.hop);   // next block, used next iteration
     // layer-1 im2col: row r (position P0-8+r) = x[r .. r+8], zero for K in [9, 16)
-    for (int r = tid; r < 128 * T1; r += 256) {
+    for (int r = gt; r < 128 * T1; r += kGroupThreads) {
       __half2 h[8];
 #pragma unroll
       for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(sX[r + 2 * e], sX[r + 2 * e + 1]);
@@ -509,33 +602,24 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       *reinterpret_cast<uint4*>(sA1 + r * 16) = *reinterpret_cast<uint4*>(&h[0]);
       *reinterpret_cast<uint4*>(sA1 + kPlaneA1 + r * 16) = *reinterpret_cast<uint4*>(&h[4]);
     }
-    fence_proxy_async_smem();
-    tmem_fence_before_sync();
-    __syncthreads();
-    tmem_fence_after_sync();
-    if (tid == 0) {
+    sync_for_mma();
+    if (gt == 0) {
+      const uint64_t bd = umma_desc(aW1, 512, 128);
       for (int t = 0; t < T1; ++t)
-        umma_f16(tm + 32 * t, umma_desc(aA1 + (uint32_t)(128 * t) * 16, kPlaneA1, 128), umma_desc(aW1, 512, 128),
-                 kIdesc, 0u);
+        umma_f16(tm + 32 * t, umma_desc(aA1 + (uint32_t)(128 * t) * 16, kPlaneA1, 128), bd, kIdesc, 0u);
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
     store_layer(T1, 128 * T2 + 8, sBias, sH1, kPlaneH1);
-    fence_proxy_async_smem();
-    tmem_fence_before_sync();
-    __syncthreads();
-    tmem_fence_after_sync();
-    if (tid == 0) issue_conv(T2, aH1, kPlaneH1, aW2);
+    sync_for_mma();
+    if (gt == 0) issue_conv(T2, aH1, kPlaneH1, aW2);
     if (!(ok = wait_mma())) break;
     store_layer(T2, p.hop + 8, sBias + kC, sH2, kPlaneH2);
-    fence_proxy_async_smem();
-    tmem_fence_before_sync();
-    __syncthreads();
-    tmem_fence_after_sync();
-    if (tid == 0) issue_conv(T3, aH2, kPlaneH2, aW3);
+    sync_for_mma();
+    if (gt == 0) issue_conv(T3, aH2, kPlaneH2, aW3);
     if (!(ok = wait_mma())) break;
     // layer 3: relu(acc + b3), channel maxima over the block (non-negative floats order as unsigned)
-    for (int t = half; t < T3; t += 2) {
+    for (int t = 0; t < T3; ++t) {
       float a[16], b[16];
       tmem_ld16(tm_lane + 32 * t, a);
       tmem_ld16(tm_lane + 32 * t + 16, b);
@@ -548,27 +632,37 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       }
     }
     tmem_fence_before_sync();
-    __syncthreads();
+    group_sync(g);
     // head: logits[w][j] = bl[j] + sum_c Wl[j][c] m[c]  (FP16 weights, FP32 sums)
-    for (int j = tid; j < p.Z; j += 256) {
-      float s = __half2float(p.w[p.obl + j]);
-      const __half* wl = p.w + p.oWl + (size_t)j * kC;
-#pragma unroll 8
-      for (int c = 0; c < kC; ++c) s = fmaf(__half2float(wl[c]), __uint_as_float(sMax[c]), s);
+    float mc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) mc[c] = __uint_as_float(sMax[c]);
+    for (int j = gt; j < p.Z; j += kGroupThreads) {
+      const __half* wl = wl_staged ? sWl + j * kC : p.w + p.oWl + (size_t)j * kC;
+      float s = wl_staged ? sBl[j] : __half2float(p.w[p.obl + j]);
+#pragma unroll
+      for (int c4 = 0; c4 < kC / 8; ++c4) {
+        const uint4 u = *reinterpret_cast<const uint4*>(wl + 8 * c4);
+        const __half2* h2 = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __half22float2(h2[e]);
+          s = fmaf(f.x, mc[8 * c4 + 2 * e], s);
+          s = fmaf(f.y, mc[8 * c4 + 2 * e + 1], s);
+        }
+      }
       p.logits[w * p.Z + j] = s;
     }
-    __syncthreads();
+    group_sync(g);   // sMax and the staging area are reused by the next block
   }
-  if (!ok) {
-    if (tid == 0) {
-      atomicOr(p.status, 1);
-      (void)mbar_wait(bar, phase ^ 1u);   // bounded wait for the MMAs still in flight
-    }
+  if (!ok && gt == 0) {
+    atomicOr(p.status, 1);
+    (void)mbar_wait(bar, phase ^ 1u);   // bounded wait for this group's MMAs still in flight
   }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  if (warp == 0) tmem_dealloc(tm, kTmemCols);
+  if (warp == 0) tmem_dealloc(*tslot, kTmemCols);
 }
 
 }  // namespace
@@ -591,8 +685,8 @@ struct fdas_zband {
   float* logits = nullptr;   // [B][Z]
   float* dlog = nullptr;     // [B][Z]
   float* loss = nullptr;     // device scalar
-  double* partial = nullptr; // power reduction partials [kSumBlocks]
-  float* scale = nullptr;    // n / sum |A|^2
+  SelectState* sel = nullptr; // median selection state
+  float* scale = nullptr;    // ln 2 / median |A|^2
   int* status = nullptr;     // bit 0: a bounded wait of the inference kernel gave up
   int step = 0;
 };
@@ -600,7 +694,7 @@ struct fdas_zband {
 namespace {
 void free_zband(fdas_zband* z) {
   void* ptrs[] = {z->p,  z->ph,     z->g,   z->m,      z->v,    z->a1,   z->a2,      z->a3,    z->d1,
-                  z->d2, z->pooled, z->arg, z->logits, z->dlog, z->loss, z->partial, z->scale, z->status};
+                  z->d2, z->pooled, z->arg, z->logits, z->dlog, z->loss, z->sel, z->scale, z->status};
   for (void* q : ptrs) cudaFree(q);
   delete z;
 }
@@ -625,10 +719,15 @@ cudaError_t forward(fdas_zband* z, const float* in, int B, bool half_weights, cu
   return cudaGetLastError();
 }
 
-// scale = n / sum |A|^2 into `scale` (fixed reduction order).
-void launch_power_scale(const float2* spec, int64_t n, double* partial, float* scale, cudaStream_t st) {
-  power_partial_kernel<<<kSumBlocks, 256, 0, st>>>(spec, n, partial);
-  power_scale_kernel<<<1, kSumBlocks, 0, st>>>(partial, n, scale);
+// scale = ln 2 / median |A|^2 into `scale`.
+void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* scale, cudaStream_t st) {
+  select_init_kernel<<<1, 256, 0, st>>>(sel, n);
+  const int64_t blocks = (n + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    select_hist_kernel<<<grid, 256, 0, st>>>(spec, n, sel, shift);
+    select_pick_kernel<<<1, 32, 0, st>>>(sel, shift, scale);
+  }
 }
 }  // namespace
 
@@ -672,7 +771,7 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
             cudaMalloc(&z->pooled, B * kC * 4) == cudaSuccess && cudaMalloc(&z->arg, B * kC * 4) == cudaSuccess &&
             cudaMalloc(&z->logits, B * (size_t)n_out * 4) == cudaSuccess &&
             cudaMalloc(&z->dlog, B * (size_t)n_out * 4) == cudaSuccess && cudaMalloc(&z->loss, 4) == cudaSuccess &&
-            cudaMalloc(&z->partial, kSumBlocks * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&z->sel, sizeof(SelectState)) == cudaSuccess &&
             cudaMalloc(&z->scale, 4) == cudaSuccess && cudaMalloc(&z->status, 4) == cudaSuccess;
   if (!ok || cudaMemset(z->p, 0, P * 4) != cudaSuccess || cudaMemset(z->ph, 0, P * 2) != cudaSuccess ||
       cudaMemset(z->m, 0, P * 4) != cudaSuccess || cudaMemset(z->v, 0, P * 4) != cudaSuccess ||
@@ -793,7 +892,7 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
     return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t nb = (n_bins + hop - 1) / hop;
-  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->partial, z->scale, st);
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->sel, z->scale, st);
   ProposeParams q;
   q.spec = reinterpret_cast<const float2*>(d_spectrum);
   q.n = n_bins;
@@ -812,7 +911,8 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
   q.n_blocks = nb;
   q.logits = d_logits;
   q.status = z->status;
-  const unsigned grid = (unsigned)(nb < z->sm_count ? nb : z->sm_count);
+  const int64_t pairs = (nb + 1) / 2;
+  const unsigned grid = (unsigned)(pairs < z->sm_count ? pairs : z->sm_count);
   propose_kernel<<<grid, 256, kProposeSmem, st>>>(q);
   return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
@@ -836,18 +936,18 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
     return FDAS_ERR_INVALID;
   if (reinterpret_cast<uintptr_t>(d_spectrum) & 7u) return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  double* partial = nullptr;
+  SelectState* sel = nullptr;
   float* scale = nullptr;
-  if (cudaMallocAsync(&partial, kSumBlocks * sizeof(double), st) != cudaSuccess) return FDAS_ERR_ALLOC;
+  if (cudaMallocAsync(&sel, sizeof(SelectState), st) != cudaSuccess) return FDAS_ERR_ALLOC;
   if (cudaMallocAsync(&scale, 4, st) != cudaSuccess) {
-    cudaFreeAsync(partial, st);
+    cudaFreeAsync(sel, st);
     return FDAS_ERR_ALLOC;
   }
-  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, partial, scale, st);
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, sel, scale, st);
   spectrum_windows_kernel<<<(unsigned)n_windows, 256, 0, st>>>(reinterpret_cast<const float2*>(d_spectrum), n_bins,
                                                                scale, window, hop, d_windows);
   const int rc = cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
-  cudaFreeAsync(partial, st);
+  cudaFreeAsync(sel, st);
   cudaFreeAsync(scale, st);
   return rc;
 }

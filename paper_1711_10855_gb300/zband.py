@@ -8,10 +8,10 @@ search stays the reference: recall is the fraction of its detections the partial
 
 Training windows and labels are made by the method itself.  Input spectra are white Gaussian
 noise series with one constant-fdot chirp in every other block (z uniform in [-zmax, zmax],
-matched-filter SNR a*sqrt(N)/2 uniform in [snr_lo, snr_hi], mean bin inside the block).  The
+matched-filter SNR a*sqrt(N)/2 log-uniform in [snr_lo, snr_hi], mean bin inside the block).  The
 full search (fdas_convolve_power) computes each spectrum's plane; a block is labelled with the
 templates within `half_band` of +-z* when the plane's maximum over the block, in units of the
-mean power, reaches DET_POWER (z* the template holding it), and with no template otherwise.
+noise power (median |A|^2 / ln 2), reaches DET_POWER (z* the template holding it), and with no template otherwise.
 The z = 0 power spectrum cannot tell z from -z (for integer q, |H_q(-z)| = |H_q(z)|), so a label
 covers both signs.
 
@@ -31,7 +31,7 @@ from . import fdas
 
 WINDOW = 1024
 HOP = WINDOW // 2
-DET_POWER = 20.0        # detection threshold on P / mean |A|^2 (noise cells are Exp(1))
+DET_POWER = 20.0        # detection threshold on P / noise power (noise cells are Exp(1))
 HALF_BAND = 6.0         # label half-width in z (bins drifted)
 
 
@@ -54,15 +54,16 @@ def band_masks(z_abs: np.ndarray, zs: np.ndarray, half_band: float) -> np.ndarra
 
 
 def chirp_blocks(rng: np.random.Generator, n_series: int, n_bins: int, zmax: float, snr, every: int = 2):
-    """Chirp parameters (r0, z, amp, phase, snr), each [n_series, K]: one chirp in blocks
-    1, 1 + every, ... (block w = bins [w*HOP, (w+1)*HOP)), mean bin in the block's middle 60%."""
+    """Chirp parameters (r0, z, amp, phase, snr, block), each [n_series, K]: one chirp in blocks
+    1, 1 + every, ... (block w = bins [w*HOP, (w+1)*HOP)), mean bin in the block's middle 60%,
+    z uniform in [-zmax, zmax], SNR log-uniform in [snr[0], snr[1]]."""
     nb = n_bins // HOP
     blocks = np.arange(1, nb - 1, every)
     K = blocks.size
     N = 2 * n_bins
     z = rng.uniform(-zmax, zmax, (n_series, K))
     rbar = blocks[None, :] * HOP + rng.uniform(0.2, 0.8, (n_series, K)) * HOP
-    s = rng.uniform(snr[0], snr[1], (n_series, K))
+    s = np.exp(rng.uniform(np.log(snr[0]), np.log(snr[1]), (n_series, K)))
     amp = 2.0 * s / np.sqrt(N)
     phase = rng.uniform(0, 2 * np.pi, (n_series, K))
     return dict(r0=rbar - 0.5 * z, z=z, amp=amp, phase=phase, snr=s, block=np.broadcast_to(blocks, (n_series, K)))
@@ -84,11 +85,18 @@ def chirp_spectra(torch, n_bins: int, chirps: dict, gen, dev):
     return torch.fft.rfft(x, dim=1)[:, :n_bins].to(torch.complex64).contiguous()
 
 
+def noise_power(torch, spectrum):
+    """Noise level of |A_r|^2: its lower median / ln 2 (the mean of exponential noise, robust to
+    signals in fewer than half of the bins)."""
+    p = spectrum.real.double() ** 2 + spectrum.imag.double() ** 2
+    return p.flatten().kthvalue((p.numel() + 1) // 2).values / np.log(2.0)
+
+
 def block_detections(torch, plane, spectrum, n_bins: int):
-    """Per block of the full plane: (max of P / mean |A|^2, template index of that maximum)."""
+    """Per block of the full plane: (max of P / noise power, template index of that maximum)."""
     Z = plane.shape[0]
     nb = -(-n_bins // HOP)
-    mean = (spectrum.real.double() ** 2 + spectrum.imag.double() ** 2).mean()
+    mean = noise_power(torch, spectrum)
     pad = nb * HOP - n_bins
     p = plane if pad == 0 else torch.nn.functional.pad(plane, (0, pad))
     blk = p.view(Z, nb, HOP).amax(dim=2)                 # [Z, nb]
@@ -97,7 +105,7 @@ def block_detections(torch, plane, spectrum, n_bins: int):
 
 
 def make_training_set(n_windows: int, zmax: int = 200, zstep: int = 2, half_band: float = HALF_BAND,
-                      snr=(5.0, 30.0), n_bins: int = 1 << 17, det_power: float = DET_POWER, seed: int = 17111,
+                      snr=(5.0, 100.0), n_bins: int = 1 << 17, det_power: float = DET_POWER, seed: int = 17111,
                       chunk: int = 16, device=None) -> TrainingSet:
     """About n_windows labelled windows (all blocks of ceil(n_windows / (n_bins/HOP)) spectra)."""
     import torch
@@ -144,8 +152,11 @@ def init_params(n_out: int, seed: int = 0, bias_out: float = -3.0) -> np.ndarray
 
 
 def train(net: "fdas.ZBand", data: TrainingSet, steps: int, batch: int = 256, lr: float = 1e-3, seed: int = 5,
-          log_every: int = 0):
-    """Adam on shuffled mini-batches; returns [(step, loss)] at the logged steps and the last."""
+          log_every: int = 0, lr_final: float | None = None):
+    """Adam on shuffled mini-batches, the learning rate decaying from lr to lr_final (default
+    lr / 20) on a half cosine; returns [(step, loss)] at the logged steps and the last."""
+    import math
+    lr_final = lr / 20.0 if lr_final is None else lr_final
     import torch
     dev = data.windows.device
     g = torch.Generator(device=dev)
@@ -163,7 +174,8 @@ def train(net: "fdas.ZBand", data: TrainingSet, steps: int, batch: int = 256, lr
         torch.index_select(data.windows, 0, idx, out=xb)
         torch.index_select(data.targets, 0, idx, out=yb)
         want = step == steps - 1 or (log_every > 0 and step % log_every == 0)
-        loss = net.train_step(xb, yb, batch, lr, want_loss=want)
+        lr_t = lr_final + (lr - lr_final) * 0.5 * (1.0 + math.cos(math.pi * step / max(1, steps - 1)))
+        loss = net.train_step(xb, yb, batch, lr_t, want_loss=want)
         if want:
             losses.append((step, loss))
     return losses

@@ -49,10 +49,26 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_spectrum_windows_match_oracle():
-    n = 5000
-    spec = synth.noise_spectrum(n, 3)
-    spec[1234] *= 40.0                                 # a bin above the cap
+def _window_case(kind):
+    if kind == "noise":
+        spec = synth.noise_spectrum(5000, 3)
+        spec[1234] *= 40.0                              # a bin above the cap
+    elif kind == "odd-ties":
+        rng = np.random.default_rng(4)
+        spec = (rng.integers(1, 4, 4099) + 0j).astype(np.complex64)   # |A|^2 in {1, 4, 9}: ties
+    elif kind == "zero-median":
+        spec = np.zeros(4096, dtype=np.complex64)
+        spec[:1000] = 3.0                               # median 0: x = 0 everywhere
+    else:
+        spec = synth.spectrum(synth.small())            # 2^16 bins with a chirp
+    return spec
+
+
+@pytest.mark.parametrize("kind", ["noise", "odd-ties", "zero-median", "chirp"])
+def test_spectrum_windows_match_oracle(kind):
+    """Windows of x: the exact median selection on the device and the cap, against the oracle."""
+    spec = _window_case(kind)
+    n = spec.size
     W, H = 1024, 512
     nw = oz.n_blocks(n, W)
     d = torch.empty((nw, W), dtype=torch.float32, device="cuda")
@@ -60,7 +76,8 @@ def test_spectrum_windows_match_oracle():
     torch.cuda.synchronize()
     want = oz.windows(oz.power_x(spec), W, H, nw)
     got = d.cpu().numpy()
-    assert got.max() == np.float32(oz.X_CAP)
+    if kind == "noise":
+        assert got.max() == np.float32(oz.X_CAP)
     np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-6)
 
 
