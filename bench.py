@@ -417,6 +417,8 @@ def run_ours(args):
         fdas_build.build()
 
     w = workload(args.workload, args.n_bins)
+    if args.seg_len:
+        w = synth.with_seg_len(w, args.seg_len)
     # each rank correlates its own spectrum (independent de-dispersion trials)
     wr = synth.Workload(w.name, w.n_samples, w.zmax, w.zstep, w.tmpl_len, w.seg_len, w.seed + 1000 * rank,
                         w.chirps)
@@ -567,6 +569,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-bins", type=int, default=None, help="profiling only: shorter spectrum, same geometry")
+    ap.add_argument("--seg-len", type=int, default=None, help="segment length sweep (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

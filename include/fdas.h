@@ -57,7 +57,7 @@ enum fdas_status {
 
 /* Limits checked by fdas_plan_create. */
 #define FDAS_MIN_SEG_LEN 256
-#define FDAS_MAX_SEG_LEN 2048
+#define FDAS_MAX_SEG_LEN 8192
 
 /*
  * Create a plan for an n_bins-bin spectrum, the z grid -zmax..zmax step zstep, segment
@@ -163,8 +163,9 @@ int fdas_segment_spectra(fdas_plan* plan, const float* d_spectrum, float* d_out,
  * Section 1) correlated by ONE persistent kernel launch.  Every spectrum i has its own n_bins[i]
  * and zmax[i]; zstep, seg_len and tmpl_len are shared.  The batch holds one template bank for the
  * largest zmax (rows for smaller zmax are its middle rows).  The flattened (spectrum, segment
- * group, template) work is split into equal contiguous ranges over the SMs.  Only segment
- * lengths with a descriptor-driven kernel are accepted (512 and 2048).
+ * group, template) work is split into equal contiguous ranges over the SMs.  Segment lengths 512
+ * and 2048 have this descriptor-driven kernel; the others (256, 1024, 4096, 8192) run one
+ * single-spectrum launch per spectrum, in order on the stream.
  * ------------------------------------------------------------------------------------------- */
 typedef struct fdas_batch fdas_batch;
 
@@ -183,20 +184,23 @@ int fdas_batch_templates_build(fdas_batch* batch, fdas_stream_t stream);
  * 16-byte-aligned device pointers.  Synchronises `stream` once (the descriptor staging is
  * reused), copies the descriptor table, then issues ONE kernel launch -- directly, or with
  * use_graph != 0 as a CUDA graph holding that launch (captured and instantiated on first use,
- * replayed afterwards).  FDAS_ERR_NOT_BUILT / INVALID / ALIGN / CUDA as fdas_convolve_power. */
+ * replayed afterwards).  Without the descriptor-driven kernel the graph holds the per-spectrum
+ * launches and is captured again whenever the pointers differ from the captured ones.
+ * FDAS_ERR_NOT_BUILT / INVALID / ALIGN / CUDA as fdas_convolve_power. */
 int fdas_batch_convolve_power(fdas_batch* batch, const float* const* d_spectra, float* const* d_planes,
                               int use_graph, fdas_stream_t stream);
 
 /* As fdas_check for the batch's status word. */
 int fdas_batch_check(fdas_batch* batch, fdas_stream_t stream);
 int fdas_batch_destroy(fdas_batch* batch);
-/* seg_len, template-bank rows, total work units, segments resident per CTA; NULL outputs skipped. */
+/* seg_len, template-bank rows, total work units, segments resident per CTA (0: one launch per
+ * spectrum); NULL outputs skipped. */
 int fdas_batch_info(const fdas_batch* batch, int* seg_len, int* z_bank, int64_t* units, int* segments_per_cta);
 
 /*
  * Autotuner (no counterpart in the paper): for each candidate segment length, build a batch,
  * time three launches on the caller's buffers with CUDA events (after one warm-up) and keep the
- * fastest; candidates that cannot serve the batch (tmpl_len > L/2, no kernel) are skipped and
+ * fastest; candidates that cannot serve the batch (tmpl_len > L/2) are skipped and
  * reported as -1 in ms_out (n_candidates floats, may be NULL).  The planes are overwritten.
  * Returns FDAS_OK with *best_seg_len set, FDAS_ERR_INVALID if no candidate applies.
  */

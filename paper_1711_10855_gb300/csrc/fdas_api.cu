@@ -112,8 +112,10 @@ __global__ void taps_kernel(double2* taps, int zmax, int zstep, int h) {
 
 // Float offset of the real part of element k in the pair-major structure-of-arrays layout
 // (lane k1 = k % n1, k2 = k / n1; pair p = k2/2 of lane k1 is the float4 at p*n1 + k1 holding
-// re(2p), re(2p+1), im(2p), im(2p+1)); the imaginary part is 2 floats further.
+// re(2p), re(2p+1), im(2p), im(2p+1)); the imaginary part is 2 floats further.  n1 = 0 is the
+// interleaved natural order, where the imaginary part is the next float.
 __host__ __device__ __forceinline__ int pair_layout_re(int k, int n1) {
+  if (n1 == 0) return 2 * k;   // natural order (L >= 4096)
   const int k1 = k % n1, k2 = k / n1;
   return ((k2 >> 1) * n1 + k1) * 4 + (k2 & 1);
 }
@@ -145,14 +147,21 @@ __global__ void spectra_kernel(const double2* taps, float2* templates, int L, in
   float* dst = reinterpret_cast<float*>(templates + (size_t)zi * L);
   const int off = pair_layout_re(k, n1);
   dst[off] = (float)(re / L);
-  dst[off + 2] = (float)(im / L);
+  dst[off + (n1 ? 2 : 1)] = (float)(im / L);
 }
 
 // Inter-pass twiddles exp(+i 2pi n2 k1 / L), n2 < N2 = L/n1, k1 < n1: lane k1's pair j holds
-// n2 = j and n2 = j + N2/2 (float4 at j*n1 + k1: re, re, im, im).
+// n2 = j and n2 = j + N2/2 (float4 at j*n1 + k1: re, re, im, im).  n1 = 0 (L >= 4096): the
+// natural table exp(-2 pi i t / L).
 __global__ void twist_kernel(float2* tw, int L, int n1) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= L) return;
+  if (n1 == 0) {   // L >= 4096: W[t] = exp(-2 pi i t / L) for the Stockham passes
+    double sn, cs;
+    sincospi(2.0 * (double)idx / (double)L, &sn, &cs);
+    tw[idx] = make_float2((float)cs, (float)-sn);
+    return;
+  }
   const int k1 = idx % n1, n2 = idx / n1;
   const int h2 = L / n1 / 2;
   double sn, cs;
@@ -205,6 +214,7 @@ EncodeTiledFn get_encode_fn() {
 // 1-D tensor map over the spectrum: n_bins elements of 8 bytes, box of min(L, 256) elements,
 // zero fill outside [0, n_bins).
 int make_spectrum_map(fdas_plan* p, const void* d_spectrum) {
+  if (p->L >= 4096) return FDAS_OK;   // the L >= 4096 kernels read the spectrum directly
   if (p->map_ptr == d_spectrum) return FDAS_OK;
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return FDAS_ERR_CUDA;
@@ -402,6 +412,7 @@ int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fd
   if (rc != FDAS_OK) return rc;
   fdas::SegParams q;
   q.twist = p->d_twist;
+  q.spectrum_in = reinterpret_cast<const float2*>(d_spectrum);
   q.out = reinterpret_cast<float2*>(d_out);
   q.status = p->d_status;
   q.n_bins = p->n_bins;
@@ -474,7 +485,7 @@ int fdas_template_spectrum(fdas_plan* p, int z_idx, float* host_out) {
   for (int k = 0; k < p->L; ++k) {
     const int off = pair_layout_re(k, p->n1);
     host_out[2 * k] = f[off];
-    host_out[2 * k + 1] = f[off + 2];
+    host_out[2 * k + 1] = f[off + (p->n1 ? 2 : 1)];
   }
   std::free(tmp);
   return FDAS_OK;
@@ -514,6 +525,7 @@ cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist
 }
 
 int encode_spectrum_map(CUtensorMap* map, const void* d_spectrum, int64_t n_bins, int L) {
+  if (L >= 4096) return FDAS_OK;   // the L >= 4096 kernels read the spectrum directly
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return FDAS_ERR_CUDA;
   cuuint64_t gdim[1] = {(cuuint64_t)n_bins};

@@ -6,6 +6,9 @@
 // of per-spectrum descriptors.  One launch of the descriptor-driven kernel correlates every
 // spectrum with its templates; the flattened (spectrum, segment group, template) work is split
 // into equal contiguous ranges over the SMs, so uneven lengths do not unbalance the grid.
+// Segment lengths without that kernel (256, 1024, 4096, 8192) run one single-spectrum launch per
+// spectrum instead, in order on the stream (as a CUDA graph of those launches with use_graph).
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -33,6 +36,9 @@ struct fdas_batch {
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // per-spectrum launches (G == 0): the pointers the graph was captured with
+  std::vector<const float*> cap_specs;
+  std::vector<float*> cap_planes;
 };
 
 namespace {
@@ -67,6 +73,39 @@ fdas::BatchParams batch_params(const fdas_batch* b) {
   return q;
 }
 
+// One single-spectrum launch per spectrum (segment lengths without the descriptor-driven
+// kernel); spectrum i uses rows z_off_i.. of the shared bank.
+cudaError_t launch_per_spectrum(const fdas_batch* b, const float* const* d_spectra, float* const* d_planes,
+                                cudaStream_t st) {
+  for (int i = 0; i < b->count; ++i) {
+    const fdas::SpecDesc& d = b->h_descs[i];
+    fdas::ConvParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.spectrum = reinterpret_cast<const float2*>(d_spectra[i]);
+    q.templates = b->d_templates + (size_t)d.z_off * b->L;
+    q.twist = b->d_twist;
+    q.plane = d_planes[i];
+    q.status = b->d_status;
+    q.n_bins = d.n_bins;
+    q.nseg = d.nseg;
+    q.units = 0;
+    q.Z = d.Z;
+    q.V = b->V;
+    q.h = b->h;
+    CUtensorMap map;
+    if (fdas::encode_spectrum_map(&map, d_spectra[i], d.n_bins, b->L) != FDAS_OK) return cudaErrorInvalidValue;
+    const cudaError_t e = fdas::launch_convolve(b->L, &map, q, b->sm_count, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_any(const fdas_batch* b, const float* const* d_spectra, float* const* d_planes,
+                       cudaStream_t st) {
+  if (b->G == 0) return launch_per_spectrum(b, d_spectra, d_planes, st);
+  return fdas::launch_batch(b->L, batch_params(b), b->sm_count, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -89,11 +128,7 @@ fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax,
     }
     if (zmax[i] > zmax_bank) zmax_bank = zmax[i];
   }
-  const int G = fdas::batch_segments_per_cta(seg_len);
-  if (G == 0) {   // no descriptor-driven kernel for this segment length
-    g_batch_error = FDAS_ERR_INVALID;
-    return nullptr;
-  }
+  const int G = fdas::batch_segments_per_cta(seg_len);   // 0: one launch per spectrum
   int ndev = 0, dev = 0, major = 0, minor = 0, sms = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -154,7 +189,7 @@ fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax,
     std::memset(&d, 0, sizeof(d));
     d.n_bins = n_bins[i];
     d.nseg = (n_bins[i] + b->V - 1) / b->V;
-    d.ngroups = (d.nseg + G - 1) / G;
+    d.ngroups = G > 0 ? (d.nseg + G - 1) / G : d.nseg;
     d.Z = 2 * (zmax[i] / zstep) + 1;
     d.z_off = (zmax_bank - zmax[i]) / zstep;
     d.unit_base = base;
@@ -189,16 +224,24 @@ int fdas_batch_convolve_power(fdas_batch* b, const float* const* d_spectra, floa
     b->h_descs[i].spec = reinterpret_cast<const float2*>(d_spectra[i]);
     b->h_descs[i].plane = d_planes[i];
   }
-  if (cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(fdas::SpecDesc) * (size_t)b->count, cudaMemcpyHostToDevice,
-                      st) != cudaSuccess)
+  if (b->G > 0 && cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(fdas::SpecDesc) * (size_t)b->count,
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FDAS_ERR_CUDA;
-  const fdas::BatchParams q = batch_params(b);
-  if (!use_graph) return fdas::launch_batch(b->L, q, b->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  if (!use_graph) return launch_any(b, d_spectra, d_planes, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  if (b->G == 0 && b->graph_exec &&
+      (!std::equal(b->cap_specs.begin(), b->cap_specs.end(), d_spectra) ||
+       !std::equal(b->cap_planes.begin(), b->cap_planes.end(), d_planes))) {
+    // per-spectrum launches hold the pointers as parameters: new pointers need a new graph
+    cudaGraphExecDestroy(b->graph_exec);
+    cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+  }
   if (!b->graph_exec) {
-    // capture the persistent launch once; its parameters (table address, sizes) never change
+    // capture once; the persistent launch's parameters (table address, sizes) never change
     if (cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return FDAS_ERR_CUDA;
-    const cudaError_t le = fdas::launch_batch(b->L, q, b->sm_count, b->capture_stream);
+    const cudaError_t le = launch_any(b, d_spectra, d_planes, b->capture_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess || !g) {
@@ -212,6 +255,8 @@ int fdas_batch_convolve_power(fdas_batch* b, const float* const* d_spectra, floa
       return FDAS_ERR_CUDA;
     }
     b->graph = g;
+    b->cap_specs.assign(d_spectra, d_spectra + b->count);
+    b->cap_planes.assign(d_planes, d_planes + b->count);
   }
   return cudaGraphLaunch(b->graph_exec, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
@@ -254,7 +299,7 @@ int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int z
   for (int c = 0; c < n_candidates; ++c) {
     if (ms_out) ms_out[c] = -1.f;
     fdas_batch* b = fdas_batch_create(count, n_bins, zmax, zstep, seg_len_candidates[c], tmpl_len);
-    if (!b) continue;   // this segment length cannot serve the batch (validation or no kernel)
+    if (!b) continue;   // this segment length cannot serve the batch (tmpl_len > L/2)
     int rc = fdas_batch_templates_build(b, stream);
     if (rc == FDAS_OK) rc = fdas_batch_convolve_power(b, d_spectra, d_planes, 0, stream);   // warm-up
     float ms = 0.f;
@@ -264,7 +309,8 @@ int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int z
       cudaEventCreate(&e1);
       const int reps = 3;
       cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && rc == FDAS_OK; ++r) rc = fdas::launch_batch(b->L, batch_params(b), b->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+      for (int r = 0; r < reps && rc == FDAS_OK; ++r)
+        rc = launch_any(b, d_spectra, d_planes, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = FDAS_ERR_CUDA;
       cudaEventElapsedTime(&ms, e0, e1);

@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(256, 1)
 // ---------------------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------------------
-int conv_group_threads(int L) { return L <= 256 ? 8 : (L <= 1024 ? 16 : 32); }
+int conv_group_threads(int L) { return L <= 256 ? 8 : (L <= 1024 ? 16 : (L <= 2048 ? 32 : 0)); }
 
 template <class Cfg>
 static cudaError_t launch_conv_cfg(const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {
@@ -884,16 +884,20 @@ cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, 
     case 512: return launch_single_desc(512, p, sm_count, st);
     case 1024: return launch_conv_cfg<Cfg1024>(map, p, sm_count, st);
     case 2048: return launch_single_desc(2048, p, sm_count, st);
+    case 4096:
+    case 8192: return launch_convolve_big(L, p, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_segment_spectra(int L, const CUtensorMap* map, const SegParams& p, int, cudaStream_t st) {
+cudaError_t launch_segment_spectra(int L, const CUtensorMap* map, const SegParams& p, int sm_count, cudaStream_t st) {
   switch (L) {
     case 256: return launch_seg_cfg<Cfg256>(map, p, st);
     case 512: return launch_seg_cfg<Cfg512>(map, p, st);
     case 1024: return launch_seg_cfg<Cfg1024>(map, p, st);
     case 2048: return launch_seg_cfg<ConvCfg<2048, 32, 2, 2>>(map, p, st);   // two-round exchange fits
+    case 4096:
+    case 8192: return launch_segment_spectra_big(L, p, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }

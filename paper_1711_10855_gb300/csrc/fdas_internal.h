@@ -49,6 +49,7 @@ struct BatchParams {
 // Parameters of the forward-transform-only kernel (steps a2 + a3, for tests).
 struct SegParams {
   const float2* twist;
+  const float2* spectrum_in; // n_bins complex64 (read directly by the L >= 4096 kernel)
   float2* out;              // nseg x L, natural order
   int* status;
   int64_t n_bins;
@@ -58,7 +59,8 @@ struct SegParams {
 
 // Threads per transform group (N1) used for segment length L; the template bank and the
 // twiddle table are stored in the layout of that decomposition (element k = k1 + N1*k2 at
-// ((k2/2)*N1 + k1)*2 + k2%2).
+// ((k2/2)*N1 + k1)*2 + k2%2).  0 for L >= 4096: natural order, and the twiddle table holds
+// exp(-2 pi i t / L), t < L (shared-memory Stockham kernel, fdas_convolve_big.cu).
 int conv_group_threads(int L);
 
 // Segments resident per CTA of the descriptor-driven kernel for segment length L, or 0 if L has
@@ -75,6 +77,9 @@ cudaError_t launch_convolve(int L, const CUtensorMap* spec_map, const ConvParams
                             cudaStream_t stream);
 cudaError_t launch_segment_spectra(int L, const CUtensorMap* spec_map, const SegParams& p,
                                    int sm_count, cudaStream_t stream);
+// Segment lengths 4096 and 8192 (fdas_convolve_big.cu); no tensor map.
+cudaError_t launch_convolve_big(int L, const ConvParams& p, int sm_count, cudaStream_t stream);
+cudaError_t launch_segment_spectra_big(int L, const SegParams& p, int sm_count, cudaStream_t stream);
 
 }  // namespace fdas
 

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -458,7 +459,9 @@ __device__ __forceinline__ int group_all(int g, int v) {
   return r;
 }
 
+template <int HOP>
 __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) {
+  static_assert(HOP % 128 == 0 && HOP <= kMaxHop, "hop");
   using namespace fdas;
   extern __shared__ __align__(1024) unsigned char sm[];
   __half* sW1 = reinterpret_cast<__half*>(sm + kOffW1);
@@ -516,8 +519,8 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
   const uint32_t aW1 = smem_u32(sW1), aW2 = smem_u32(sW2), aW3 = smem_u32(sW3);
   const uint32_t aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aA1 = smem_u32(sA1);
   const float sc = *p.scale;
-  const int T3 = p.hop / 128, T2 = T3 + 1, T1 = T2 + 1;
-  const int nx = 128 * T1 + 8;
+  constexpr int T3 = HOP / 128, T2 = T3 + 1, T1 = T2 + 1;
+  constexpr int nx = 128 * T1 + 8;
   uint32_t phase = 0;
   bool ok = true;
 
@@ -531,9 +534,10 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       xa[e] = (j < nx && r >= 0 && r < p.n) ? __ldg(p.spec + r) : make_float2(0.f, 0.f);
     }
   };
-  // wait for this group's committed MMAs; every thread of the group, bounded
+  // wait for this group's committed MMAs: one thread polls (bounded), the others sleep in the
+  // group's hardware barrier
   auto wait_mma = [&]() -> bool {
-    const int good = group_all(g, mbar_wait(bar, phase) ? 1 : 0);
+    const int good = group_all(g, gt == 0 ? (mbar_wait(bar, phase) ? 1 : 0) : 1);
     phase ^= 1u;
     tmem_fence_after_sync();
     return good != 0;
@@ -567,22 +571,30 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       }
     }
   };
-  // one k = 9 convolution layer: ntiles M-tiles, A rows start at 128t + k in the source planes;
-  // tiles innermost, so consecutive MMAs feed independent accumulators
-  auto issue_conv = [&](int ntiles, uint32_t src, uint32_t plane, uint32_t wts) {
-    for (int k = 0; k < kK; ++k)
-      for (int c = 0; c < 2; ++c) {
-        const uint64_t bd = umma_desc(wts + k * 2048 + c * 1024, 512, 128);
-        for (int t = 0; t < ntiles; ++t)
-          umma_f16(tm + 32 * t, umma_desc(src + (uint32_t)(128 * t + k) * 16 + 2 * c * plane, plane, 128), bd,
-                   kIdesc, (k | c) != 0);
-      }
+  // one k = 9 convolution layer: NT M-tiles, A rows start at 128t + k in the source planes;
+  // tiles innermost, so consecutive MMAs feed independent accumulators.  A descriptor's start
+  // address is its low field, so every operand is a base descriptor plus a constant.
+  auto issue_conv = [&](auto ntiles, uint32_t src, uint32_t plane, uint32_t wts) {
+    constexpr int NT = decltype(ntiles)::value;
+    const uint64_t a0 = umma_desc(src, plane, 128), b0 = umma_desc(wts, 512, 128);
+    static_for<kK>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      static_for<2>([&](auto cc) {
+        constexpr int c = decltype(cc)::value;
+        const uint64_t bd = b0 + (uint64_t)((k * 2048 + c * 1024) >> 4);
+        const uint64_t ac = a0 + (uint64_t)(((uint32_t)k * 16 + 2u * c * plane) >> 4);
+        static_for<NT>([&](auto tt) {
+          constexpr int t = decltype(tt)::value;
+          umma_f16(tm + 32 * t, ac + (uint64_t)(128 * t), bd, kIdesc, (k | c) != 0);
+        });
+      });
+    });
     umma_commit(bar);
   };
 
   const int64_t wstep = 2 * (int64_t)gridDim.x;
   int64_t w = 2 * (int64_t)blockIdx.x + g;
-  if (w < p.n_blocks) load_x(w * p.hop);
+  if (w < p.n_blocks) load_x(w * HOP);
   for (; w < p.n_blocks; w += wstep) {
 #pragma unroll
     for (int e = 0; e < kXPer; ++e) {
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     }
     if (gt < kC) sMax[gt] = 0u;
     group_sync(g);
-    if (w + wstep < p.n_blocks) load_x((w + wstep) * p.hop);   // next block, used next iteration
+    if (w + wstep < p.n_blocks) load_x((w + wstep) * HOP);   // next block, used next iteration
     // layer-1 im2col: row r (position P0-8+r) = x[r .. r+8], zero for K in [9, 16)
     for (int r = gt; r < 128 * T1; r += kGroupThreads) {
       __half2 h[8];
@@ -604,19 +616,21 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     }
     sync_for_mma();
     if (gt == 0) {
-      const uint64_t bd = umma_desc(aW1, 512, 128);
-      for (int t = 0; t < T1; ++t)
-        umma_f16(tm + 32 * t, umma_desc(aA1 + (uint32_t)(128 * t) * 16, kPlaneA1, 128), bd, kIdesc, 0u);
+      const uint64_t bd = umma_desc(aW1, 512, 128), a0 = umma_desc(aA1, kPlaneA1, 128);
+      static_for<T1>([&](auto tt) {
+        constexpr int t = decltype(tt)::value;
+        umma_f16(tm + 32 * t, a0 + (uint64_t)(128 * t), bd, kIdesc, 0u);   // 128 rows x 16 B = 2048 B
+      });
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
     store_layer(T1, 128 * T2 + 8, sBias, sH1, kPlaneH1);
     sync_for_mma();
-    if (gt == 0) issue_conv(T2, aH1, kPlaneH1, aW2);
+    if (gt == 0) issue_conv(std::integral_constant<int, T2>{}, aH1, kPlaneH1, aW2);
     if (!(ok = wait_mma())) break;
-    store_layer(T2, p.hop + 8, sBias + kC, sH2, kPlaneH2);
+    store_layer(T2, HOP + 8, sBias + kC, sH2, kPlaneH2);
     sync_for_mma();
-    if (gt == 0) issue_conv(T3, aH2, kPlaneH2, aW3);
+    if (gt == 0) issue_conv(std::integral_constant<int, T3>{}, aH2, kPlaneH2, aW3);
     if (!(ok = wait_mma())) break;
     // layer 3: relu(acc + b3), channel maxima over the block (non-negative floats order as unsigned)
     for (int t = 0; t < T3; ++t) {
@@ -750,7 +764,13 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
                            (int)conv_fwd_smem<kC>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_bwd_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdDataSmem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(propose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+      cudaFuncSetAttribute(propose_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(propose_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(propose_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(propose_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
           cudaSuccess) {
     cudaGetLastError();
     return nullptr;
@@ -913,7 +933,12 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
   q.status = z->status;
   const int64_t pairs = (nb + 1) / 2;
   const unsigned grid = (unsigned)(pairs < z->sm_count ? pairs : z->sm_count);
-  propose_kernel<<<grid, 256, kProposeSmem, st>>>(q);
+  switch (hop) {
+    case 128: propose_kernel<128><<<grid, 256, kProposeSmem, st>>>(q); break;
+    case 256: propose_kernel<256><<<grid, 256, kProposeSmem, st>>>(q); break;
+    case 384: propose_kernel<384><<<grid, 256, kProposeSmem, st>>>(q); break;
+    default: propose_kernel<512><<<grid, 256, kProposeSmem, st>>>(q); break;
+  }
   return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 

@@ -56,7 +56,7 @@ def test_error_strings(lib):
     (4096, 200000, 1, 512, 64), # Z > 65535
     (4096, 20, 2, 500, 64),     # not a power of two
     (4096, 20, 2, 128, 64),     # below the minimum segment
-    (4096, 20, 2, 8192, 64),    # above the maximum segment
+    (4096, 20, 2, 16384, 64),   # above the maximum segment
     (4096, 20, 2, 512, 2),      # m < 4
     (4096, 20, 2, 512, 66),     # m % 4
     (4096, 20, 2, 512, 260),    # m > L/2
@@ -104,7 +104,9 @@ def test_batch_create_validation_without_device(lib):
     assert lib.fdas_batch_last_error() == -1
     assert not create(2, np.array([4096, 8190], dtype=np.int64), z, 2, 2048, 512)   # n % 4
     assert lib.fdas_batch_last_error() == -1
-    assert not create(2, n, z, 2, 1024, 256)   # no descriptor-driven kernel for L = 1024
+    assert not create(2, n, z, 2, 16384, 512)   # above the maximum segment length
+    assert lib.fdas_batch_last_error() == -1
+    assert not create(2, n, z, 2, 1024, 516)    # m > L/2
     assert lib.fdas_batch_last_error() == -1
     assert lib.fdas_batch_destroy(None) == 0
     assert lib.fdas_batch_check(None, None) == -1

@@ -35,8 +35,9 @@ def _check_rows(got, ref):
     assert np.all(err <= ROW_TOL * scale), float(np.max(err / scale))
 
 
-@pytest.mark.parametrize("L,m", [(2048, 512), (512, 64)])
+@pytest.mark.parametrize("L,m", [(2048, 512), (512, 64), (1024, 256), (4096, 512)])
 def test_batch_matches_oracle_direct_and_graph(dev, L, m):
+    """512 and 2048: one persistent launch; 1024 and 4096: one launch per spectrum."""
     from paper_1711_10855_gb300 import fdas
     n_bins = [4000, 20004, 1536 * 5, 100, 9000, 3072]
     zmax = [20, 10, 20, 4, 16, 12]
@@ -125,14 +126,45 @@ def test_batch_dedispersion_trials_sampled(dev):
                 assert abs(r0 - 40 + dr - c.r_mean) <= 1.0, (i, c, r0 - 40 + dr)
 
 
+def test_per_spectrum_batch_graph_follows_new_pointers(dev):
+    """Without the descriptor-driven kernel the graph holds the pointers: new buffers must be
+    served by a new capture, not by the old graph."""
+    import torch
+    from paper_1711_10855_gb300 import fdas
+    n_bins, zmax = [9000, 4000], [8, 4]
+    specs = [synth.noise_spectrum(n, seed=300 + i) for i, n in enumerate(n_bins)]
+    with fdas.Batch(n_bins, zmax, 2, 4096, 512) as b:
+        assert b.segments_per_cta == 0
+        b.build_templates()
+        d1, p1 = _tensors(specs, b.n_z, dev)
+        b.convolve_power(d1, p1, use_graph=True)
+        d2, p2 = _tensors(specs, b.n_z, dev)                      # new buffers, same data
+        b.convolve_power(d2, p2, use_graph=True)
+        b.check()
+        for a, c in zip(p1, p2):
+            assert torch.equal(a, c)
+
+
+def test_autotune_over_1024_2048_4096(dev):
+    from paper_1711_10855_gb300 import fdas
+    n_bins, zmax = [50000, 20000, 8000], [20, 10, 20]
+    specs = [synth.noise_spectrum(n, seed=i) for i, n in enumerate(n_bins)]
+    d, planes = _tensors(specs, [2 * (z // 2) + 1 for z in zmax], dev)
+    cands = [1024, 2048, 4096]
+    best, ms = fdas.batch_autotune(n_bins, zmax, 2, 512, cands, d, planes)
+    assert all(x > 0 for x in ms), ms
+    assert best == cands[int(np.argmin(ms))]
+    for spec, z, p in zip(specs, zmax, planes):   # the planes hold the last candidate's result
+        _check_rows(p.cpu().numpy().astype(np.float64), oracle.plane_rows(spec, z, 2, 512))
+
+
 def test_autotune_picks_a_serving_segment_length(dev):
     from paper_1711_10855_gb300 import fdas
     n_bins, zmax = [50000, 20000, 8000], [20, 10, 20]
     specs = [synth.noise_spectrum(n, seed=i) for i, n in enumerate(n_bins)]
     d, planes = _tensors(specs, [2 * (z // 2) + 1 for z in zmax], dev)
     best, ms = fdas.batch_autotune(n_bins, zmax, 2, 64, [512, 1024, 2048], d, planes)
-    assert best in (512, 2048)
-    assert ms[1] == -1.0 and ms[0] > 0 and ms[2] > 0
-    assert ms[[512, 1024, 2048].index(best)] == min(x for x in ms if x > 0)
+    assert all(x > 0 for x in ms)
+    assert ms[[512, 1024, 2048].index(best)] == min(ms)
     best, ms = fdas.batch_autotune(n_bins, zmax, 2, 512, [512, 2048], d, planes)
-    assert best == 2048 and ms[0] == -1.0
+    assert best == 2048 and ms[0] == -1.0     # m = 512 > L/2 at L = 512: cannot serve
