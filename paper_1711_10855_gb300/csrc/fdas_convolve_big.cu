@@ -1,16 +1,18 @@
 // fdas_convolve_big.cu -- the fused correlation (steps a2..a7 of Eq. 2 by overlap-and-save,
 // Section 2) for segment lengths 4096 and 8192.
 //
-// One CTA of 512 threads owns a segment at a time: it loads the segment (zeros outside [0, n)),
+// One CTA of L/16 threads owns a segment at a time: it loads the segment (zeros outside [0, n)),
 // transforms it (forward, Eq. 3 sign) into shared memory once, and then for every template z
 // multiplies by T_z, inverse-transforms and stores |y|^2 of the first V outputs.  Transforms are
-// Stockham autosort FFTs in shared memory (ping-pong between two L-point buffers): radix-4
-// passes, plus one radix-2 pass when log2 L is odd.  Pass p combines sub-transforms of length Ns
-// into length R*Ns: butterfly j (j < L/R) reads elements j + r*L/R, multiplies element r by
-// W^(r*k*L/(R*Ns)) (k = j mod Ns, W = exp(-+2 pi i / L) from the plan's twiddle table), takes the
-// R-point DFT and writes element r to (j - k)*R + k + r*Ns.  The first pass of an inverse
-// transform reads X*T directly and the last pass writes powers to the plane, so each template
-// costs log_4 L passes over shared memory.  Templates are stored in natural order.
+// Stockham autosort FFTs in shared memory (ping-pong between two L-point buffers): radix-16
+// passes (each thread one 16-point DFT in registers), plus one radix-2 pass when log16 L is not
+// whole.  Pass p combines sub-transforms of length Ns into length R*Ns: butterfly j (j < L/R)
+// reads elements j + r*L/R, multiplies element r by W^(r*k*L/(R*Ns)) (k = j mod Ns,
+// W = exp(-+2 pi i / L), from a quarter-period table in shared memory staged from the plan's
+// twiddle table), takes the R-point DFT and writes element r to (j - k)*R + k + r*Ns.  The first
+// pass of an inverse transform reads X*T directly and the last pass writes powers to the plane.
+// Shared buffers hold element i at i + i/16, so the stride-16 writes of the first pass spread
+// over the banks.  Templates are stored in natural order.
 #include <cuda_runtime.h>
 
 #include "fdas_device.cuh"
@@ -19,100 +21,105 @@
 namespace fdas {
 namespace {
 
-constexpr int kBigThreads = 512;
+constexpr int kRadix = 16;
 
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
+__host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 
-// W^t for the forward transform (DIR = -1), its conjugate for the inverse (DIR = +1).
-template <int DIR>
-__device__ __forceinline__ float2 twiddle(const float2* W, int t) {
-  float2 w = __ldg(W + t);
+template <int L>
+struct BigCfg {
+  static constexpr int NT = L / kRadix;                 // threads per CTA
+  static constexpr int P16 = ilog2c(L) / 4;             // radix-16 passes
+  static constexpr bool R2 = (ilog2c(L) % 4) == 1;      // one radix-2 pass after them
+  static constexpr int P = P16 + (R2 ? 1 : 0);
+  static constexpr int BUF = padded(L);                 // padded buffer length (float2)
+  static_assert(ilog2c(L) % 4 == 0 || R2, "L = 16^p or 2 * 16^p");
+};
+
+// W^t for the forward transform (DIR = -1), its conjugate for the inverse (DIR = +1), from the
+// quarter-period table Q[u] = W^u, u < L/4: W^(u + q L/4) = (-i)^q W^u.
+template <int L, int DIR>
+__device__ __forceinline__ float2 twiddle(const float2* Q, int t) {
+  const float2 b = Q[t & (L / 4 - 1)];
+  const int q = (t / (L / 4)) & 3;
+  float2 w = (q & 1) ? make_float2(b.y, -b.x) : b;   // -i * b for odd quadrants
+  if (q & 2) w = make_float2(-w.x, -w.y);
   if (DIR > 0) w.y = -w.y;
   return w;
 }
 
-// One radix-4 pass with sub-transform length Ns.
-template <int L, int DIR, class Load, class Store>
-__device__ __forceinline__ void pass4(int Ns, const float2* W, Load load, Store store) {
-  for (int j = threadIdx.x; j < L / 4; j += kBigThreads) {
+// One radix-R pass with sub-transform length Ns (R = 16 or 2).
+template <int L, int R, int DIR, class Load, class Store>
+__device__ __forceinline__ void pass_r(int Ns, const float2* Q, Load load, Store store) {
+  constexpr int NT = BigCfg<L>::NT, LOGR = ilog2c(R);
+  for (int j = threadIdx.x; j < L / R; j += NT) {
     const int k = j & (Ns - 1);
-    const int t = k * (L / (4 * Ns));
-    float2 v0 = load(j), v1 = load(j + L / 4), v2 = load(j + L / 2), v3 = load(j + 3 * L / 4);
-    if (Ns > 1) {
-      v1 = cmulf(v1, twiddle<DIR>(W, t));
-      v2 = cmulf(v2, twiddle<DIR>(W, 2 * t));
-      v3 = cmulf(v3, twiddle<DIR>(W, 3 * t));
-    }
-    const float2 a0 = make_float2(v0.x + v2.x, v0.y + v2.y), a1 = make_float2(v0.x - v2.x, v0.y - v2.y);
-    const float2 a2 = make_float2(v1.x + v3.x, v1.y + v3.y), a3 = make_float2(v1.x - v3.x, v1.y - v3.y);
-    const float2 y0 = make_float2(a0.x + a2.x, a0.y + a2.y), y2 = make_float2(a0.x - a2.x, a0.y - a2.y);
-    // forward: y1 = a1 - i a3, y3 = a1 + i a3; inverse: the two swap
-    const float2 ym = make_float2(a1.x + a3.y, a1.y - a3.x), yp = make_float2(a1.x - a3.y, a1.y + a3.x);
-    const int d = ((j - k) << 2) + k;
-    store(d, y0);
-    store(d + Ns, DIR < 0 ? ym : yp);
-    store(d + 2 * Ns, y2);
-    store(d + 3 * Ns, DIR < 0 ? yp : ym);
+    const int t = k * (L / (R * Ns));
+    float2 v[R];
+    static_for<R>([&](auto rr) {
+      constexpr int r = decltype(rr)::value;
+      float2 x = load(j + r * (L / R));
+      if (r > 0 && Ns > 1) x = cmul(x, twiddle<L, DIR>(Q, r * t));
+      v[bitrev(r, LOGR)] = x;
+    });
+    fft_dit<R, DIR>(v);
+    const int d = (j - k) * R + k;
+    static_for<R>([&](auto rr) {
+      constexpr int r = decltype(rr)::value;
+      store(d + r * Ns, v[r]);
+    });
   }
 }
-
-// The final radix-2 pass (Ns = L/2, so k = j and the twiddle index is j).
-template <int L, int DIR, class Load, class Store>
-__device__ __forceinline__ void pass2(const float2* W, Load load, Store store) {
-  for (int j = threadIdx.x; j < L / 2; j += kBigThreads) {
-    const float2 v0 = load(j), v1 = cmulf(load(j + L / 2), twiddle<DIR>(W, j));
-    store(j, make_float2(v0.x + v1.x, v0.y + v1.y));
-    store(j + L / 2, make_float2(v0.x - v1.x, v0.y - v1.y));
-  }
-}
-
-__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
 
 // A whole L-point transform: `first` supplies the input, `last` consumes the output (natural
-// order); b0 / b1 are the ping-pong buffers.  Ends with a CTA barrier.
+// order); b0 / b1 are the padded ping-pong buffers.  Ends with a CTA barrier.
 template <int L, int DIR, class First, class Last>
-__device__ __forceinline__ void stockham(float2* b0, float2* b1, const float2* W, First first, Last last) {
-  constexpr int P4 = ilog2c(L) / 2;
-  constexpr bool R2 = (ilog2c(L) & 1) != 0;
-  constexpr int P = P4 + (R2 ? 1 : 0);
-  auto ld = [](const float2* b) { return [b](int i) { return b[i]; }; };
-  auto st = [](float2* b) { return [b](int i, float2 v) { b[i] = v; }; };
-  static_for<P>([&](auto pp) {
+__device__ __forceinline__ void stockham(float2* b0, float2* b1, const float2* Q, First first, Last last) {
+  using C = BigCfg<L>;
+  auto ld = [](const float2* b) { return [b](int i) { return b[padded(i)]; }; };
+  auto st = [](float2* b) { return [b](int i, float2 v) { b[padded(i)] = v; }; };
+  static_for<C::P>([&](auto pp) {
     constexpr int p = decltype(pp)::value;
     float2* src = (p % 2 == 1) ? b0 : b1;
     float2* dst = (p % 2 == 0) ? b0 : b1;
-    if constexpr (p < P4) {
-      constexpr int Ns = 1 << (2 * p);
-      if constexpr (p == 0 && p == P - 1) pass4<L, DIR>(Ns, W, first, last);
-      else if constexpr (p == 0) pass4<L, DIR>(Ns, W, first, st(dst));
-      else if constexpr (p == P - 1) pass4<L, DIR>(Ns, W, ld(src), last);
-      else pass4<L, DIR>(Ns, W, ld(src), st(dst));
+    if constexpr (p < C::P16) {
+      constexpr int Ns = 1 << (4 * p);
+      if constexpr (p == 0) pass_r<L, kRadix, DIR>(Ns, Q, first, st(dst));
+      else if constexpr (p == C::P - 1) pass_r<L, kRadix, DIR>(Ns, Q, ld(src), last);
+      else pass_r<L, kRadix, DIR>(Ns, Q, ld(src), st(dst));
     } else {
-      pass2<L, DIR>(W, ld(src), last);
+      pass_r<L, 2, DIR>(L / 2, Q, ld(src), last);
     }
     __syncthreads();
   });
 }
 
+// The first L/4 entries of the plan's twiddle table into shared memory.
 template <int L>
-__global__ void __launch_bounds__(kBigThreads, 1) convolve_big_kernel(const ConvParams p) {
+__device__ __forceinline__ void stage_quarter(float2* Q, const float2* twist) {
+  for (int u = threadIdx.x; u < L / 4; u += BigCfg<L>::NT) Q[u] = __ldg(twist + u);
+  __syncthreads();
+}
+
+template <int L>
+__global__ void __launch_bounds__(BigCfg<L>::NT) convolve_big_kernel(const ConvParams p) {
+  using C = BigCfg<L>;
   extern __shared__ __align__(16) float2 sbig[];
   float2* X = sbig;
-  float2* b0 = sbig + L;
-  float2* b1 = sbig + 2 * L;
-  const float2* W = p.twist;
+  float2* b0 = sbig + C::BUF;
+  float2* b1 = sbig + 2 * C::BUF;
+  float2* Q = sbig + 3 * C::BUF;
+  stage_quarter<L>(Q, p.twist);
   for (int64_t s = blockIdx.x; s < p.nseg; s += gridDim.x) {
     const int64_t x0 = s * (int64_t)p.V - p.h;
     // a2 + a3: the segment (zeros outside [0, n)), forward transform into X
     stockham<L, -1>(
-        b0, b1, W,
+        b0, b1, Q,
         [&](int i) {
           const int64_t r = x0 + i;
           return (r >= 0 && r < p.n_bins) ? __ldg(p.spectrum + r) : make_float2(0.f, 0.f);
         },
-        [&](int i, float2 v) { X[i] = v; });
+        [&](int i, float2 v) { X[padded(i)] = v; });
     const int64_t segbase = s * (int64_t)p.V;
     const int64_t lim64 = p.n_bins - segbase < (int64_t)p.V ? p.n_bins - segbase : (int64_t)p.V;
     const int lim = (int)lim64;
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) convolve_big_kernel(const Conv
       float* row = p.plane + (size_t)z * p.n_bins + segbase;
       // a4 + a5 + a6 + a7: X*T_z, inverse transform, keep n < V, store |y|^2
       stockham<L, +1>(
-          b0, b1, W, [&](int i) { return cmulf(X[i], __ldg(T + i)); },
+          b0, b1, Q, [&](int i) { return cmul(X[padded(i)], __ldg(T + i)); },
           [&](int i, float2 v) {
             if (i < lim) __stcs(row + i, fmaf(v.x, v.x, v.y * v.y));
           });
@@ -131,15 +138,18 @@ __global__ void __launch_bounds__(kBigThreads, 1) convolve_big_kernel(const Conv
 
 // Forward transforms only (a2 + a3), natural order, for tests of the FFT.
 template <int L>
-__global__ void __launch_bounds__(kBigThreads, 1) segment_spectra_big_kernel(const SegParams p) {
+__global__ void __launch_bounds__(BigCfg<L>::NT) segment_spectra_big_kernel(const SegParams p) {
+  using C = BigCfg<L>;
   extern __shared__ __align__(16) float2 sbig[];
   float2* b0 = sbig;
-  float2* b1 = sbig + L;
+  float2* b1 = sbig + C::BUF;
+  float2* Q = sbig + 2 * C::BUF;
+  stage_quarter<L>(Q, p.twist);
   for (int64_t s = blockIdx.x; s < p.nseg; s += gridDim.x) {
     const int64_t x0 = s * (int64_t)p.V - p.h;
     float2* out = p.out + (size_t)s * L;
     stockham<L, -1>(
-        b0, b1, p.twist,
+        b0, b1, Q,
         [&](int i) {
           const int64_t r = x0 + i;
           return (r >= 0 && r < p.n_bins) ? __ldg(p.spectrum_in + r) : make_float2(0.f, 0.f);
@@ -150,23 +160,28 @@ __global__ void __launch_bounds__(kBigThreads, 1) segment_spectra_big_kernel(con
 
 template <int L>
 cudaError_t launch_big(const ConvParams& p, int sm_count, cudaStream_t st) {
-  constexpr size_t smem = 3 * (size_t)L * sizeof(float2);
+  using C = BigCfg<L>;
+  constexpr size_t smem = (3 * (size_t)C::BUF + L / 4) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(convolve_big_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int per_sm = (int)(227 * 1024 / smem) > 0 ? (int)(227 * 1024 / smem) : 1;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, convolve_big_kernel<L>, C::NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
   const int64_t grid = p.nseg < (int64_t)per_sm * sm_count ? p.nseg : (int64_t)per_sm * sm_count;
-  convolve_big_kernel<L><<<(unsigned)grid, kBigThreads, smem, st>>>(p);
+  convolve_big_kernel<L><<<(unsigned)grid, C::NT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int L>
 cudaError_t launch_seg_big(const SegParams& p, int sm_count, cudaStream_t st) {
-  constexpr size_t smem = 2 * (size_t)L * sizeof(float2);
+  using C = BigCfg<L>;
+  constexpr size_t smem = (2 * (size_t)C::BUF + L / 4) * sizeof(float2);
   cudaError_t e =
       cudaFuncSetAttribute(segment_spectra_big_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = p.nseg < (int64_t)sm_count ? p.nseg : (int64_t)sm_count;
-  segment_spectra_big_kernel<L><<<(unsigned)grid, kBigThreads, smem, st>>>(p);
+  segment_spectra_big_kernel<L><<<(unsigned)grid, C::NT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
