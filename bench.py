@@ -390,7 +390,7 @@ def run_zband(args):
                      "achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                      "frac": tflops / float(peaks["bf16_tflops"]),
                      "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
-                     "flops_per_launch": 2.0 * macs, "traffic": None},
+                     "flops_per_launch": 2.0 * macs, "traffic": zband_traffic()},
         "clocks": clk.summary(), "gpu_launches": args.steps * 5,
     }
     print(json.dumps(line), flush=True)
@@ -543,6 +543,25 @@ def run_ours(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def zband_kernel_rev() -> str:
+    """Content hash of the z-band kernel sources (ncu traffic of the inference kernel)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("fdas_zband.cu", "fdas_umma.cuh", "fdas_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1711_10855_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def zband_traffic():
+    path = os.path.join(ROOT, "profiles", "traffic_zband.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        tj = json.load(f)
+    return tj.get("dram_bytes_per_launch") if tj.get("kernel_rev") == zband_kernel_rev() else None
 
 
 def kernel_rev() -> str:
