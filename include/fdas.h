@@ -100,7 +100,10 @@ int fdas_templates_build(fdas_plan* plan, fdas_stream_t stream);
  *   d_spectrum  n_bins complex64 values (interleaved re, im floats), device memory, 16-byte
  *               aligned, read-only, caller-owned.
  *   d_plane     Z x n_bins float32, row-major (row z_idx = (z + zmax)/zstep, pitch n_bins),
- *               device memory, 16-byte aligned, caller-owned; every element is overwritten.
+ *               16-byte aligned, caller-owned; every element is overwritten.  Device memory,
+ *               or pinned host memory (cudaHostAlloc / cudaHostRegister, addressable by the
+ *               device): the kernel then stores the plane straight into host memory over the
+ *               host link, overlapping the transfer with the computation.
  *
  * Asynchronous: no host synchronisation and no allocation.  Returns FDAS_ERR_NOT_BUILT before
  * fdas_templates_build, FDAS_ERR_INVALID for NULL pointers, FDAS_ERR_ALIGN for misaligned

@@ -548,13 +548,21 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     group_sync(g);
     tmem_fence_after_sync();
   };
-  // accumulator tile t (lanes = rows 128t + 32q + lane) + bias -> relu -> FP16 planes, rows < limit
-  auto store_layer = [&](int ntiles, int limit, const float* bias, unsigned char* dst, uint32_t plane) {
-    for (int t = 0; t < ntiles; ++t) {
-      float a[16], b[16];
-      tmem_ld16(tm_lane + 32 * t, a);
-      tmem_ld16(tm_lane + 32 * t + 16, b);
+  // accumulator tile t (lanes = rows 128t + 32q + lane) + bias -> relu -> FP16 planes, rows < limit.
+  // The next tile's TMEM load is issued before this tile is converted (tcgen05.wait::ld waits for
+  // every earlier load, so the wait comes first and the two buffers alternate).
+  auto store_layer = [&](auto ntiles, int limit, const float* bias, unsigned char* dst, uint32_t plane) {
+    constexpr int NT = decltype(ntiles)::value;
+    float a[2][16], b[2][16];
+    tmem_ld16(tm_lane, a[0]);
+    tmem_ld16(tm_lane + 16, b[0]);
+    static_for<NT>([&](auto tt) {
+      constexpr int t = decltype(tt)::value, cur = t & 1;
       tmem_wait_ld();
+      if constexpr (t + 1 < NT) {
+        tmem_ld16(tm_lane + 32 * (t + 1), a[cur ^ 1]);
+        tmem_ld16(tm_lane + 32 * (t + 1) + 16, b[cur ^ 1]);
+      }
       const int r = 128 * t + 32 * q + lane;
       if (r < limit) {
 #pragma unroll
@@ -563,13 +571,13 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int c = 8 * j + 2 * e;
-            const float v0 = c < 16 ? a[c] : b[c - 16], v1 = c + 1 < 16 ? a[c + 1] : b[c - 15];
+            const float v0 = c < 16 ? a[cur][c] : b[cur][c - 16], v1 = c + 1 < 16 ? a[cur][c + 1] : b[cur][c - 15];
             h[e] = __floats2half2_rn(fmaxf(v0 + bias[c], 0.f), fmaxf(v1 + bias[c + 1], 0.f));
           }
           *reinterpret_cast<uint4*>(dst + j * plane + r * 16) = *reinterpret_cast<uint4*>(h);
         }
       }
-    }
+    });
   };
   // one k = 9 convolution layer: NT M-tiles, A rows start at 128t + k in the source planes;
   // tiles innermost, so consecutive MMAs feed independent accumulators.  A descriptor's start
@@ -624,24 +632,36 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-    store_layer(T1, 128 * T2 + 8, sBias, sH1, kPlaneH1);
+    store_layer(std::integral_constant<int, T1>{}, 128 * T2 + 8, sBias, sH1, kPlaneH1);
     sync_for_mma();
     if (gt == 0) issue_conv(std::integral_constant<int, T2>{}, aH1, kPlaneH1, aW2);
     if (!(ok = wait_mma())) break;
-    store_layer(T2, HOP + 8, sBias + kC, sH2, kPlaneH2);
+    store_layer(std::integral_constant<int, T2>{}, HOP + 8, sBias + kC, sH2, kPlaneH2);
     sync_for_mma();
     if (gt == 0) issue_conv(std::integral_constant<int, T3>{}, aH2, kPlaneH2, aW3);
     if (!(ok = wait_mma())) break;
-    // layer 3: relu(acc + b3), channel maxima over the block (non-negative floats order as unsigned)
-    for (int t = 0; t < T3; ++t) {
-      float a[16], b[16];
-      tmem_ld16(tm_lane + 32 * t, a);
-      tmem_ld16(tm_lane + 32 * t + 16, b);
-      tmem_wait_ld();
+    // layer 3: relu(acc + b3), channel maxima over the block: each thread keeps the maximum of
+    // its rows, then one warp reduction per channel (non-negative floats order as unsigned)
+    {
+      float mx[kC];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) mx[c] = 0.f;
+      float a[2][16], b[2][16];
+      tmem_ld16(tm_lane, a[0]);
+      tmem_ld16(tm_lane + 16, b[0]);
+      static_for<T3>([&](auto tt) {
+        constexpr int t = decltype(tt)::value, cur = t & 1;
+        tmem_wait_ld();
+        if constexpr (t + 1 < T3) {
+          tmem_ld16(tm_lane + 32 * (t + 1), a[cur ^ 1]);
+          tmem_ld16(tm_lane + 32 * (t + 1) + 16, b[cur ^ 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < kC; ++c) mx[c] = fmaxf(mx[c], (c < 16 ? a[cur][c] : b[cur][c - 16]) + sBias[2 * kC + c]);
+      });
 #pragma unroll
       for (int c = 0; c < kC; ++c) {
-        const float v = fmaxf((c < 16 ? a[c] : b[c - 16]) + sBias[2 * kC + c], 0.f);
-        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(mx[c], 0.f)));
         if (lane == c) atomicMax(&sMax[c], m);
       }
     }

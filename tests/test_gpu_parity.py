@@ -157,6 +157,24 @@ def test_plane_edge_cases(dev, n, zmax, zstep, L, m):
     assert_rows_close(got, ref)
 
 
+def test_plane_into_pinned_host_memory(dev):
+    """The plane may live in pinned host memory: the kernel stores it over the host link, and
+    the result equals the device-memory plane bit for bit."""
+    import torch
+    fdas = _fdas()
+    n = 50000
+    spec = synth.noise_spectrum(n, seed=12)
+    with fdas.Plan(n, 20, 2, 2048, 512) as plan:
+        plan.build_templates()
+        d = to_device(spec, dev)
+        on_dev = torch.empty((plan.n_z, n), dtype=torch.float32, device=dev)
+        on_host = torch.full((plan.n_z, n), float("nan"), dtype=torch.float32).pin_memory()
+        plan.convolve_power(d, on_dev)
+        plan.convolve_power(d, on_host)
+        plan.check()
+        assert torch.equal(on_dev.cpu(), on_host)
+
+
 def test_plane_overwrites_every_cell_and_is_deterministic(dev):
     import torch
     fdas = _fdas()
