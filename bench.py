@@ -247,7 +247,7 @@ def run_batch(args):
              for n in n_bins]
     planes = [torch.empty((int(z), int(n)), dtype=torch.float32, device=dev) for z, n in zip(n_z, n_bins)]
     stream = torch.cuda.current_stream(dev)
-    candidates = [512, 1024, 2048]
+    candidates = [1024, 2048, 4096]
     best, tune_ms = fdas.batch_autotune(n_bins, zmax, zstep, m, candidates, specs, planes, stream)
     b = fdas.Batch(n_bins, zmax, zstep, best, m)
     b.build_templates(stream)

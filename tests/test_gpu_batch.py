@@ -35,9 +35,9 @@ def _check_rows(got, ref):
     assert np.all(err <= ROW_TOL * scale), float(np.max(err / scale))
 
 
-@pytest.mark.parametrize("L,m", [(2048, 512), (512, 64), (1024, 256), (4096, 512)])
+@pytest.mark.parametrize("L,m", [(2048, 512), (512, 64), (1024, 256), (4096, 512), (256, 64), (8192, 1024)])
 def test_batch_matches_oracle_direct_and_graph(dev, L, m):
-    """512 and 2048: one persistent launch; 1024 and 4096: one launch per spectrum."""
+    """512 and 2048: one persistent launch; 256, 1024, 4096 and 8192: one launch per spectrum."""
     from paper_1711_10855_gb300 import fdas
     n_bins = [4000, 20004, 1536 * 5, 100, 9000, 3072]
     zmax = [20, 10, 20, 4, 16, 12]

@@ -83,6 +83,10 @@ def test_static_entry_matches_plan_entry_on_two_calls(dev):
     got2 = _static_plane(d2, n2, 40, 2, 2048, 512, dev)
     ref2 = _plan_plane(d2, n2, 40, 2, 2048, 512, dev)
     _assert_rows_close(got2, ref2)
+    # call 3: a long segment (4096, shared-memory Stockham kernel, natural-order bank)
+    got3 = _static_plane(d2, n2, 20, 2, 4096, 512, dev)
+    ref3 = _plan_plane(d2, n2, 20, 2, 4096, 512, dev)
+    _assert_rows_close(got3, ref3)
 
 
 def test_static_entry_rejects_geometry_beyond_the_array(dev):
