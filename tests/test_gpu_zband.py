@@ -128,7 +128,7 @@ def test_train_step_gradients_and_adam_match_oracle():
     np.testing.assert_allclose(v, v_o, rtol=3e-5, atol=1e-15)
 
 
-@pytest.mark.parametrize("W,n_bins", [(1024, 512 * 3 + 100), (1024, 40000), (512, 9000), (256, 3000)])
+@pytest.mark.parametrize("W,n_bins", [(1024, 512 * 3 + 100), (1024, 40000), (768, 20000), (512, 9000), (256, 3000)])
 def test_propose_matches_oracle_block_logits(W, n_bins):
     """Fused tensor-core inference (FP16 weights and activations, FP32 accumulation) against the
     FP64 windowed definition with the same FP16 weights; ragged last block included."""
