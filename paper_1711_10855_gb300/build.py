@@ -2,8 +2,8 @@
 
     python -m paper_1711_10855_gb300.build
 
-Both translation units compile in parallel; the shared library links the CUDA runtime
-statically, so it depends only on the driver.  A content hash of the sources and flags is
+The translation units compile in parallel; the shared library links the CUDA runtime
+statically, so it depends only on the CUDA driver.  A content hash of the sources and flags is
 kept next to the library and the build is skipped when nothing changed.
 """
 from __future__ import annotations

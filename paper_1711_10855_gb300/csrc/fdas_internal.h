@@ -1,4 +1,4 @@
-// fdas_internal.h -- declarations shared by the two translation units of libfdas.
+// fdas_internal.h -- declarations shared by the translation units of libfdas.
 #pragma once
 
 #include <cstdint>
@@ -14,7 +14,7 @@ struct ConvParams {
   const float2* templates;  // Z x L template spectra, per-template layout of the IFFT's first pass
   const float2* twist;      // L inter-pass twiddles exp(+i 2pi n2 k1 / L), same layout
   float* plane;             // Z x n_bins output, row pitch n_bins
-  int* status;              // device status word (bit 0: a bounded wait gave up)
+  int* status;              // device status word (bit 0: a bounded wait gave up; bit 1: bad work list)
   int64_t n_bins;
   int64_t nseg;             // ceil(n_bins / V)
   int64_t units;            // (number of segment groups) x Z
@@ -37,7 +37,7 @@ struct SpecDesc {
 struct BatchParams {
   const float2* templates;  // Z_bank x L template spectra (pair-major layout)
   const float2* twist;      // L inter-pass twiddles (pair-major layout)
-  int* status;              // device status word (bit 0: a bounded wait gave up)
+  int* status;              // device status word (bit 0: a bounded wait gave up; bit 1: bad work list)
   const SpecDesc* descs;    // device table of `count` spectra, or nullptr: use `single`
   SpecDesc single;
   int count;
