@@ -229,9 +229,31 @@ def batch_workload(count: int, seed: int = 171110857):
     return n, zmax
 
 
+def batch_spectra(torch, n_bins, zmax, m: int, dev, seed: int = 171110858):
+    """Batch inputs on the device: for spectrum i, 2*n_bins[i] unit Gaussian samples plus 0-4
+    chirps (r0 uniform in [m, n-m-200], z uniform in [-0.9 zmax_i, 0.9 zmax_i], amplitude uniform in
+    [0.01, 0.05]), phases in FP64, real FFT with the Nyquist bin dropped, complex64."""
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    specs = []
+    for n, zm in zip(n_bins, zmax):
+        N = 2 * int(n)
+        x = torch.randn(N, generator=gen, device=dev, dtype=torch.float64)
+        u = torch.arange(N, device=dev, dtype=torch.float64) / N
+        for _ in range(int(rng.integers(0, 5))):
+            r0 = rng.uniform(m, int(n) - m - 200)
+            z = rng.uniform(-0.9 * zm, 0.9 * zm)
+            a = rng.uniform(0.01, 0.05)
+            x += a * torch.cos(2 * np.pi * (r0 * u + 0.5 * z * u * u) + rng.uniform(0, 2 * np.pi))
+        specs.append(torch.view_as_real(torch.fft.rfft(x)[: int(n)].to(torch.complex64)).reshape(-1).contiguous())
+        del x, u
+    return specs
+
+
 def run_batch(args):
-    """One persistent CUDA-graph launch over a batch of uneven spectra per step (complex Gaussian
-    noise spectra generated on the device from a seeded generator; the kernel is data-independent)."""
+    """One persistent CUDA-graph launch over a batch of uneven spectra per step (Gaussian-noise
+    time series with 0-4 injected chirps each, synthesised on the device from a seeded generator)."""
     import torch
     from paper_1711_10855_gb300 import build as fdas_build
     from paper_1711_10855_gb300 import fdas
@@ -241,10 +263,7 @@ def run_batch(args):
     n_bins, zmax = batch_workload(args.batch_count)
     zstep, m = 2, 512
     n_z = 2 * (zmax // zstep) + 1
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(171110857)
-    specs = [torch.randn(int(2 * n), generator=gen, device=dev, dtype=torch.float32) * float(np.sqrt(n))
-             for n in n_bins]
+    specs = batch_spectra(torch, n_bins, zmax, m, dev)
     planes = [torch.empty((int(z), int(n)), dtype=torch.float32, device=dev) for z, n in zip(n_z, n_bins)]
     stream = torch.cuda.current_stream(dev)
     candidates = [1024, 2048, 4096]
@@ -274,7 +293,7 @@ def run_batch(args):
         "metric": "f-fdot cells/s, batched de-dispersion trials (one persistent CUDA-graph launch)",
         "value": cells / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded complex Gaussian spectra on the device)",
+        "data": "synthetic (Gaussian-noise series with 0-4 injected chirps each, synthesised on the device)",
         "config": {"workload": f"batch-{args.batch_count}-uneven", "spectra": int(args.batch_count),
                    "n_bins_min": int(n_bins.min()), "n_bins_max": int(n_bins.max()), "cells": cells,
                    "zmax_set": [100, 200], "zstep": zstep, "tmpl_len": m, "seg_len": best,
@@ -309,7 +328,7 @@ def run_zband(args):
     torch.cuda.set_device(dev)
     fdas_build.build()
     t0 = time.time()
-    data = zb.make_training_set(args.zband_windows)
+    data = zb.make_training_set(args.zband_windows, snr=tuple(args.zband_snr), snr_dist=args.zband_snr_dist)
     n_windows, n_detected = int(data.windows.shape[0]), int(data.n_detected)
     net = fdas.ZBand(zb.WINDOW, 201, 256)
     net.set_params(zb.init_params(201, seed=1))
@@ -380,6 +399,7 @@ def run_zband(args):
         "data": "synthetic (survey spectrum; training windows labelled by the full search)",
         "config": {"workload": w.name + "-zband", "n_bins": w.n_bins, "n_z": plan.n_z, "window": zb.WINDOW,
                    "hop": hop, "threshold": thr, "train_windows": n_windows, "train_detected": n_detected,
+                   "train_snr": list(args.zband_snr), "train_snr_dist": args.zband_snr_dist,
                    "train_steps": args.zband_steps, "train_s": train_s, "final_loss": losses[-1][1],
                    "l2": "512 MiB buffer written between timed steps",
                    "timing": "host wall clock around the synchronised path (it reads the list length)"},
@@ -583,7 +603,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["survey", "small", "batch", "zband"], default="survey")
-    ap.add_argument("--zband-windows", type=int, default=200_000)
+    ap.add_argument("--zband-windows", type=int, default=100_000)
+    ap.add_argument("--zband-snr", type=float, nargs=2, default=[5.0, 30.0])
+    ap.add_argument("--zband-snr-dist", choices=["uniform", "log-uniform"], default="uniform")
     ap.add_argument("--zband-steps", type=int, default=8000)
     ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.05, 0.08, 0.1])
     ap.add_argument("--batch-count", type=int, default=256)

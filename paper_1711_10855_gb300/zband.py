@@ -8,7 +8,8 @@ search stays the reference: recall is the fraction of its detections the partial
 
 Training windows and labels are made by the method itself.  Input spectra are white Gaussian
 noise series with one constant-fdot chirp in every other block (z uniform in [-zmax, zmax],
-matched-filter SNR a*sqrt(N)/2 log-uniform in [snr_lo, snr_hi], mean bin inside the block).  The
+matched-filter SNR a*sqrt(N)/2 uniform in [snr_lo, snr_hi] (5-30 by default) or log-uniform,
+mean bin inside the block).  The
 full search (fdas_convolve_power) computes each spectrum's plane; a block is labelled with the
 templates within `half_band` of +-z* when the plane's maximum over the block, in units of the
 noise power (median |A|^2 / ln 2), reaches DET_POWER (z* the template holding it), and with no template otherwise.
@@ -53,17 +54,21 @@ def band_masks(z_abs: np.ndarray, zs: np.ndarray, half_band: float) -> np.ndarra
     return (d <= half_band).astype(np.float32)
 
 
-def chirp_blocks(rng: np.random.Generator, n_series: int, n_bins: int, zmax: float, snr, every: int = 2):
+def chirp_blocks(rng: np.random.Generator, n_series: int, n_bins: int, zmax: float, snr, every: int = 2,
+                 snr_dist: str = "uniform"):
     """Chirp parameters (r0, z, amp, phase, snr, block), each [n_series, K]: one chirp in blocks
     1, 1 + every, ... (block w = bins [w*HOP, (w+1)*HOP)), mean bin in the block's middle 60%,
-    z uniform in [-zmax, zmax], SNR log-uniform in [snr[0], snr[1]]."""
+    z uniform in [-zmax, zmax], SNR uniform (or log-uniform) in [snr[0], snr[1]]."""
     nb = n_bins // HOP
     blocks = np.arange(1, nb - 1, every)
     K = blocks.size
     N = 2 * n_bins
     z = rng.uniform(-zmax, zmax, (n_series, K))
     rbar = blocks[None, :] * HOP + rng.uniform(0.2, 0.8, (n_series, K)) * HOP
-    s = np.exp(rng.uniform(np.log(snr[0]), np.log(snr[1]), (n_series, K)))
+    if snr_dist == "log-uniform":
+        s = np.exp(rng.uniform(np.log(snr[0]), np.log(snr[1]), (n_series, K)))
+    else:
+        s = rng.uniform(snr[0], snr[1], (n_series, K))
     amp = 2.0 * s / np.sqrt(N)
     phase = rng.uniform(0, 2 * np.pi, (n_series, K))
     return dict(r0=rbar - 0.5 * z, z=z, amp=amp, phase=phase, snr=s, block=np.broadcast_to(blocks, (n_series, K)))
@@ -105,8 +110,8 @@ def block_detections(torch, plane, spectrum, n_bins: int):
 
 
 def make_training_set(n_windows: int, zmax: int = 200, zstep: int = 2, half_band: float = HALF_BAND,
-                      snr=(5.0, 100.0), n_bins: int = 1 << 17, det_power: float = DET_POWER, seed: int = 17111,
-                      chunk: int = 16, device=None) -> TrainingSet:
+                      snr=(5.0, 30.0), n_bins: int = 1 << 17, det_power: float = DET_POWER, seed: int = 17111,
+                      chunk: int = 16, device=None, snr_dist: str = "uniform") -> TrainingSet:
     """About n_windows labelled windows (all blocks of ceil(n_windows / (n_bins/HOP)) spectra)."""
     import torch
     dev = device or torch.device("cuda")
@@ -122,7 +127,7 @@ def make_training_set(n_windows: int, zmax: int = 200, zstep: int = 2, half_band
     wins, tgts, n_det = [], [], 0
     for s0 in range(0, n_series, chunk):
         S = min(chunk, n_series - s0)
-        specs = chirp_spectra(torch, n_bins, chirp_blocks(rng, S, n_bins, zmax, snr), gen, dev)
+        specs = chirp_spectra(torch, n_bins, chirp_blocks(rng, S, n_bins, zmax, snr, snr_dist=snr_dist), gen, dev)
         for s in range(S):
             spec = specs[s]
             plan.convolve_power(spec, plane)
