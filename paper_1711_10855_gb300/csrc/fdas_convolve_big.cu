@@ -37,10 +37,10 @@ struct BigCfg {
 };
 
 // W^t for the forward transform (DIR = -1), its conjugate for the inverse (DIR = +1), from the
-// quarter-period table Q[u] = W^u, u < L/4: W^(u + q L/4) = (-i)^q W^u.
+// quarter-period table Q[u] = W^u, u < L/4 (at padded(u)): W^(u + q L/4) = (-i)^q W^u.
 template <int L, int DIR>
 __device__ __forceinline__ float2 twiddle(const float2* Q, int t) {
-  const float2 b = Q[t & (L / 4 - 1)];
+  const float2 b = Q[padded(t & (L / 4 - 1))];   // the table is bank-padded like the buffers
   const int q = (t / (L / 4)) & 3;
   float2 w = (q & 1) ? make_float2(b.y, -b.x) : b;   // -i * b for odd quadrants
   if (q & 2) w = make_float2(-w.x, -w.y);
@@ -58,10 +58,24 @@ __device__ __forceinline__ void pass_r(int Ns, const float2* Q, Load load, Store
     float2 v[R];
     static_for<R>([&](auto rr) {
       constexpr int r = decltype(rr)::value;
-      float2 x = load(j + r * (L / R));
-      if (r > 0 && Ns > 1) x = cmul(x, twiddle<L, DIR>(Q, r * t));
-      v[bitrev(r, LOGR)] = x;
+      v[bitrev(r, LOGR)] = load(j + r * (L / R));
     });
+    if (Ns > 1) {
+      // W^(r t) for r = 1..R-1 from W^t by products of depth <= 4 (one table read per butterfly:
+      // reading every power would put a half-warp's stride-16r indices on one bank)
+      float2 w[R];
+      w[1] = twiddle<L, DIR>(Q, t);
+      static_for<R - 2>([&](auto ii) {
+        constexpr int r = decltype(ii)::value + 2;
+        constexpr int hi = 1 << (ilog2c(r));      // largest power of two <= r
+        if constexpr (hi == r) w[r] = cmul(w[r / 2], w[r / 2]);
+        else w[r] = cmul(w[hi], w[r - hi]);
+      });
+      static_for<R - 1>([&](auto ii) {
+        constexpr int r = decltype(ii)::value + 1;
+        v[bitrev(r, LOGR)] = cmul(v[bitrev(r, LOGR)], w[r]);
+      });
+    }
     fft_dit<R, DIR>(v);
     const int d = (j - k) * R + k;
     static_for<R>([&](auto rr) {
@@ -97,7 +111,7 @@ __device__ __forceinline__ void stockham(float2* b0, float2* b1, const float2* Q
 // The first L/4 entries of the plan's twiddle table into shared memory.
 template <int L>
 __device__ __forceinline__ void stage_quarter(float2* Q, const float2* twist) {
-  for (int u = threadIdx.x; u < L / 4; u += BigCfg<L>::NT) Q[u] = __ldg(twist + u);
+  for (int u = threadIdx.x; u < L / 4; u += BigCfg<L>::NT) Q[padded(u)] = __ldg(twist + u);
   __syncthreads();
 }
 
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(BigCfg<L>::NT) segment_spectra_big_kernel(cons
 template <int L>
 cudaError_t launch_big(const ConvParams& p, int sm_count, cudaStream_t st) {
   using C = BigCfg<L>;
-  constexpr size_t smem = (3 * (size_t)C::BUF + L / 4) * sizeof(float2);
+  constexpr size_t smem = (3 * (size_t)C::BUF + padded(L / 4)) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(convolve_big_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -176,7 +190,7 @@ cudaError_t launch_big(const ConvParams& p, int sm_count, cudaStream_t st) {
 template <int L>
 cudaError_t launch_seg_big(const SegParams& p, int sm_count, cudaStream_t st) {
   using C = BigCfg<L>;
-  constexpr size_t smem = (2 * (size_t)C::BUF + L / 4) * sizeof(float2);
+  constexpr size_t smem = (2 * (size_t)C::BUF + padded(L / 4)) * sizeof(float2);
   cudaError_t e =
       cudaFuncSetAttribute(segment_spectra_big_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
