@@ -1,0 +1,61 @@
+"""bench.py without a GPU: the reference arm's JSON line, the algorithmic byte and flop counts the
+roofline divides by, and the batch workload's shape."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1711_10855_gb300 import synth  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3
+    assert d["higher_is_better"] is True and d["config"]["workload"] == synth.small().name
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_algorithmic_counts_of_the_survey_plane():
+    """4 B per cell of plane, the segments with their overlap, the template bank and twiddles; flops
+    5 L log2 L + 6 L + 3 V per (segment, template) plus one forward transform per segment."""
+    w = synth.survey()
+    V = w.seg_len - w.tmpl_len
+    nseg = -(-w.n_bins // V)
+    assert nseg == 2731
+    a = bench.algorithmic(w, nseg)
+    assert a["bytes_plane"] == 4 * 201 * (1 << 22)
+    assert a["bytes"] == 4 * 201 * (1 << 22) + 8 * 2731 * 2048 + 8 * 201 * 2048 + 8 * 2048
+    assert abs(a["bytes"] / 1e9 - 3.420) < 1e-3
+    assert a["flops"] == 2731 * 201 * (5 * 2048 * 11 + 6 * 2048 + 3 * 1536) + 2731 * 5 * 2048 * 11
+    assert abs(a["flops"] / 1e9 - 71.41) < 0.01
+
+
+def test_batch_workload_shape():
+    n, zmax = bench.batch_workload(256)
+    assert n.size == zmax.size == 256
+    assert np.all(n % 4 == 0) and n.min() >= (1 << 18) - 4 and n.max() <= 1 << 22
+    assert set(np.unique(zmax)) <= {100, 200}
+    n2, z2 = bench.batch_workload(256)
+    np.testing.assert_array_equal(n, n2)
+    np.testing.assert_array_equal(zmax, z2)
+
+
+def test_replica_throughput_counts_every_rank_over_the_slowest():
+    assert bench.replica_throughput(1000, 5, 4, 2.0) == 1000 * 5 * 4 / 2.0
+    assert bench.max_over_ranks(3.5) == 3.5
