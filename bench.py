@@ -455,9 +455,16 @@ def run_ours(args):
     d_spec = torch.from_numpy(spec.view(np.float32).copy()).to(dev)
     plane = torch.empty((plan.n_z, w.n_bins), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tc = args.precision != "f32"
+
+    def correlate(out):
+        if tc:
+            plan.convolve_power_tc(d_spec, out, args.precision, stream)
+        else:
+            plan.convolve_power(d_spec, out, stream)
 
     for _ in range(args.warmup):
-        plan.convolve_power(d_spec, plane, stream)
+        correlate(plane)
         flush.fill_(1.0)
     plan.check(stream)
 
@@ -471,7 +478,7 @@ def run_ours(args):
         for e0, e1 in evs:
             flush.fill_(1.0)                     # L2 flush between timed steps, outside the events
             e0.record(stream)
-            plan.convolve_power(d_spec, plane, stream)
+            correlate(plane)
             e1.record(stream)
         torch.cuda.synchronize(dev)
     plan.check(stream)
@@ -490,7 +497,7 @@ def run_ours(args):
     e2e_steps = max(1, min(args.steps, 5))
     for _ in range(1):
         d_spec.copy_(h_spec, non_blocking=True)
-        plan.convolve_power(d_spec, h_plane, stream)
+        correlate(h_plane)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -498,7 +505,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         d_spec.copy_(h_spec, non_blocking=True)
-        plan.convolve_power(d_spec, h_plane, stream)
+        correlate(h_plane)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     plan.check(stream)
@@ -529,7 +536,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if not tc else f"{args.precision}x3+f32", "data": "synthetic",
         "config": {"workload": w.name, "n_bins": w.n_bins, "n_z": plan.n_z, "zmax": w.zmax, "zstep": w.zstep,
                    "seg_len": w.seg_len, "tmpl_len": w.tmpl_len, "n_seg": plan.n_seg,
                    "parallelism": f"replicas{world}",
@@ -550,6 +557,8 @@ def run_ours(args):
         "template_build_ms": template_build_ms,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
+    if tc:
+        tc_roofline(torch, plan, w, d_spec, stream, ms, line, peaks, peak_src)
     del h_plane, plane, flush
     torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
@@ -565,6 +574,41 @@ def run_ours(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def tc_flops(nseg: int, Z: int) -> int:
+    """Tensor flops of the DFT-matrix inverse transforms per call: for each (segment, template) a
+    64-point DFT of 32 columns as a real GEMM (32 rows, N = 128, K = 128) and a 32-point DFT of 64
+    columns (64 rows, N = 64, K = 64), each as three products (hi hi, hi lo, lo hi)."""
+    per = 3 * (2 * 32 * 128 * 128 + 2 * 64 * 64 * 64)
+    return nseg * Z * per
+
+
+def tc_roofline(torch, plan, w, d_spec, stream, step_ms, line, peaks, peak_src):
+    """The tensor-core path's line: a step is two launches (forward segment transforms in FP32,
+    then the tensor-core kernel); the forward launch is timed on its own and taken off the step
+    to give the tensor-core kernel's duration."""
+    seg = torch.empty((plan.n_seg, w.seg_len * 2), dtype=torch.float32, device=d_spec.device)
+    reps = 10
+    plan.segment_spectra(d_spec, seg, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.segment_spectra(d_spec, seg, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(d_spec.device)
+    fwd_ms = e0.elapsed_time(e1) / reps
+    kern_ms = max(step_ms - fwd_ms, 1e-6)
+    flops = tc_flops(plan.n_seg, plan.n_z)
+    peak = float(peaks["bf16_tflops"])
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    line["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
+                        "flops_per_launch": flops, "kernel_ms": kern_ms, "forward_ms": fwd_ms}
+    line["gpu_launches"] = 2 * line["steps"]
+    line["config"]["precision"] = f"inverse transforms on tensor cores, {line['dtype']}"
+    del seg
 
 
 def zband_kernel_rev() -> str:
@@ -613,6 +657,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-bins", type=int, default=None, help="profiling only: shorter spectrum, same geometry")
     ap.add_argument("--seg-len", type=int, default=None, help="segment length sweep (default: the workload's)")
+    ap.add_argument("--precision", choices=["f32", "bf16", "fp16"], default="f32",
+                    help="f32: FP32 FFT path; bf16 / fp16: inverse transforms on the tensor cores (hi + lo split)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

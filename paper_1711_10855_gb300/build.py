@@ -26,7 +26,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["fdas_api.cu", "fdas_convolve.cu", "fdas_convolve_big.cu", "fdas_static.cu", "fdas_batch.cu",
-           "fdas_zband.cu"]
+           "fdas_zband.cu", "fdas_tc.cu"]
 HEADERS = ["fdas_device.cuh", "fdas_internal.h", "fdas_umma.cuh"]
 
 

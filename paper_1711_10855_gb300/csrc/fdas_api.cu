@@ -27,6 +27,12 @@ struct fdas_plan {
   bool built = false;
   const void* map_ptr = nullptr;     // spectrum pointer the cached tensor map describes
   CUtensorMap map;
+  // tensor-core variant (fdas_convolve_power_tc), allocated on its first call
+  float2* tc_bank = nullptr;         // Z x L natural-order template spectra
+  float2* tc_seg = nullptr;          // nseg x L forward segment spectra of the current call
+  unsigned char* tc_mats = nullptr;  // DFT matrices, BF16 then FP16
+  unsigned* tc_tmax = nullptr;
+  bool tc_ready = false;
 };
 
 namespace {
@@ -233,7 +239,20 @@ int make_spectrum_map(fdas_plan* p, const void* d_spectrum) {
   return FDAS_OK;
 }
 
+void free_tc_memory(fdas_plan* p) {
+  cudaFree(p->tc_bank);
+  cudaFree(p->tc_seg);
+  cudaFree(p->tc_mats);
+  cudaFree(p->tc_tmax);
+  p->tc_bank = nullptr;
+  p->tc_seg = nullptr;
+  p->tc_mats = nullptr;
+  p->tc_tmax = nullptr;
+  p->tc_ready = false;
+}
+
 void free_plan_memory(fdas_plan* p) {
+  free_tc_memory(p);
   cudaFree(p->d_templates);
   cudaFree(p->d_taps);
   cudaFree(p->d_twist);
@@ -347,6 +366,7 @@ int fdas_templates_build(fdas_plan* p, fdas_stream_t stream) {
   twist_kernel<<<(p->L + 255) / 256, 256, 0, st>>>(p->d_twist, p->L, p->n1);
   if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;
   p->built = true;
+  p->tc_ready = false;   // the tensor-core variant copies the bank again on its next call
   return FDAS_OK;
 }
 
@@ -422,6 +442,48 @@ int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fd
   cudaError_t e =
       fdas::launch_segment_spectra(p->L, &p->map, q, p->sm_count, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_convolve_power_tc(fdas_plan* p, const float* d_spectrum, float* d_plane, int precision,
+                           fdas_stream_t stream) {
+  if (!p || !d_spectrum || !d_plane || (precision != FDAS_TC_BF16 && precision != FDAS_TC_FP16))
+    return FDAS_ERR_INVALID;
+  if (!p->built) return FDAS_ERR_NOT_BUILT;
+  if (p->L != 2048) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u))
+    return FDAS_ERR_ALIGN;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!p->tc_ready) {
+    free_tc_memory(p);
+    const int mb = fdas::tc_matrices_bytes();
+    if (cudaMalloc(&p->tc_bank, sizeof(float2) * (size_t)p->Z * p->L) != cudaSuccess ||
+        cudaMalloc(&p->tc_seg, sizeof(float2) * (size_t)p->nseg * p->L) != cudaSuccess ||
+        cudaMalloc(&p->tc_mats, 2 * (size_t)mb) != cudaSuccess ||
+        cudaMalloc(&p->tc_tmax, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      free_tc_memory(p);
+      return FDAS_ERR_ALLOC;
+    }
+    if (fdas::launch_tc_prepare(p->d_templates, p->Z, p->tc_bank, p->tc_tmax, p->tc_mats, p->tc_mats + mb, st) !=
+        cudaSuccess)
+      return FDAS_ERR_CUDA;
+    p->tc_ready = true;
+  }
+  const int rc = fdas_segment_spectra(p, d_spectrum, reinterpret_cast<float*>(p->tc_seg), stream);
+  if (rc != FDAS_OK) return rc;
+  fdas::TcParams q;
+  q.seg = p->tc_seg;
+  q.bank = p->tc_bank;
+  q.twist = p->d_twist;
+  q.mats = p->tc_mats + (precision == FDAS_TC_FP16 ? fdas::tc_matrices_bytes() : 0);
+  q.tmax = p->tc_tmax;
+  q.plane = d_plane;
+  q.status = p->d_status;
+  q.n_bins = p->n_bins;
+  q.units = p->nseg * (int64_t)((p->Z + 3) / 4);
+  q.Z = p->Z;
+  q.V = p->V;
+  return fdas::launch_tc(q, precision, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 int fdas_check(fdas_plan* p, fdas_stream_t stream) {

@@ -59,3 +59,9 @@ def test_batch_workload_shape():
 def test_replica_throughput_counts_every_rank_over_the_slowest():
     assert bench.replica_throughput(1000, 5, 4, 2.0) == 1000 * 5 * 4 / 2.0
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_tensor_core_flop_count():
+    """Per (segment, template): 3 x (2*32*128*128 + 2*64*64*64) = 4,718,592 tensor flops."""
+    assert bench.tc_flops(1, 1) == 4_718_592
+    assert abs(bench.tc_flops(2731, 201) / 1e12 - 2.590) < 1e-3
