@@ -483,6 +483,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
     plan.check(stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    accuracy = tc_accuracy(torch, plan, w, d_spec, plane, stream) if tc else None
     ms = sum(step_ms) / len(step_ms)
     t_max = max_over_ranks(sum(step_ms) / 1e3, dev)
     cells = plan.n_z * w.n_bins
@@ -559,6 +560,7 @@ def run_ours(args):
     }
     if tc:
         tc_roofline(torch, plan, w, d_spec, stream, ms, line, peaks, peak_src)
+        line["accuracy"] = accuracy
     del h_plane, plane, flush
     torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
@@ -576,6 +578,28 @@ def run_ours(args):
     return 0
 
 
+def tc_accuracy(torch, plan, w, d_spec, plane, stream) -> dict:
+    """Per-row error of the tensor-core plane against the FP32 path's (max over the row of the
+    absolute difference over the row's peak), and recovery of the injected chirps: the argmax of
+    each chirp's +-64-bin window must lie within one zstep and one bin of (z, mean r)."""
+    ref = torch.empty_like(plane)
+    plan.convolve_power(d_spec, ref, stream)
+    plan.check(stream)
+    err = ((plane - ref).abs().amax(dim=1) / ref.amax(dim=1)).cpu().numpy()
+    zs = np.arange(-w.zmax, w.zmax + 1, w.zstep)
+    found = 0
+    for c in w.chirps:
+        r0 = int(round(c.r_mean))
+        lo, hi = max(r0 - 64, 0), min(r0 + 65, w.n_bins)
+        win = plane[:, lo:hi].cpu().numpy()
+        zi, dr = np.unravel_index(np.argmax(win), win.shape)
+        found += int(abs(zs[zi] - c.z) <= w.zstep + 1e-9 and abs(lo + dr - c.r_mean) <= 1.0)
+    del ref
+    return {"vs": "FP32 path plane (itself within 1e-5 per row of the FP64 oracle in the tests)",
+            "max_row_rel_err": float(err.max()), "median_row_rel_err": float(np.median(err)),
+            "rows": int(err.size), "chirps_recovered": found, "chirps": len(w.chirps)}
+
+
 def tc_flops(nseg: int, Z: int) -> int:
     """Tensor flops of the DFT-matrix inverse transforms per call: for each (segment, template) a
     64-point DFT of 32 columns as a real GEMM (32 rows, N = 128, K = 128) and a 32-point DFT of 64
@@ -585,16 +609,17 @@ def tc_flops(nseg: int, Z: int) -> int:
 
 
 def tc_roofline(torch, plan, w, d_spec, stream, step_ms, line, peaks, peak_src):
-    """The tensor-core path's line: a step is two launches (forward segment transforms in FP32,
-    then the tensor-core kernel); the forward launch is timed on its own and taken off the step
-    to give the tensor-core kernel's duration."""
+    """The tensor-core path's line: a step is two launches (the forward segment transforms, then
+    the correlation, both on the tensor cores); the forward launch is timed on its own and taken
+    off the step to give the correlation kernel's duration."""
     seg = torch.empty((plan.n_seg, w.seg_len * 2), dtype=torch.float32, device=d_spec.device)
     reps = 10
-    plan.segment_spectra(d_spec, seg, stream)
+    precision = line["dtype"].split("x")[0]
+    plan.segment_spectra_tc(d_spec, seg, precision, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        plan.segment_spectra(d_spec, seg, stream)
+        plan.segment_spectra_tc(d_spec, seg, precision, stream)
     e1.record(stream)
     torch.cuda.synchronize(d_spec.device)
     fwd_ms = e0.elapsed_time(e1) / reps
@@ -602,13 +627,30 @@ def tc_roofline(torch, plan, w, d_spec, stream, step_ms, line, peaks, peak_src):
     flops = tc_flops(plan.n_seg, plan.n_z)
     peak = float(peaks["bf16_tflops"])
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic_tc.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("workload") == w.name and tj.get("kernel_rev") == tc_kernel_rev():
+            traffic = tj.get("dram_bytes_per_launch")
     line["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": traffic,
                         "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
                         "flops_per_launch": flops, "kernel_ms": kern_ms, "forward_ms": fwd_ms}
     line["gpu_launches"] = 2 * line["steps"]
     line["config"]["precision"] = f"inverse transforms on tensor cores, {line['dtype']}"
     del seg
+
+
+def tc_kernel_rev() -> str:
+    """Content hash of the tensor-core correlation kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("fdas_tc.cu", "fdas_umma.cuh", "fdas_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1711_10855_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def zband_kernel_rev() -> str:

@@ -115,22 +115,31 @@ int fdas_convolve_power(fdas_plan* plan, const float* d_spectrum, float* d_plane
                         fdas_stream_t stream);
 
 /*
- * The correlation with the inverse segment transforms on the tensor cores (a reduced-precision
- * variant; the paper has no counterpart): for segment length 2048 only, each inverse FFT is a
- * 64-point DFT, a twist and a 32-point DFT done as DFT-matrix contractions (tcgen05 MMAs) with
- * BF16 (precision FDAS_TC_BF16) or FP16 (FDAS_TC_FP16) operands split into hi + lo parts and FP32
- * accumulation; the forward segment transforms use the FP32 path (once per segment, reused by
- * every template) and the DFT matrices are built in FP64.  Same inputs, outputs and error codes
- * as fdas_convolve_power (FDAS_ERR_INVALID also for seg_len != 2048 or another precision).  The
- * first call on a plan (and the first after fdas_templates_build) allocates and fills a workspace
- * of Z*L*8 + nseg*L*8 + 156 KB bytes; later calls allocate nothing.  Two kernel launches on
- * `stream`.  Per-row error against the FP64 definition is a few 1e-6 of the row peak (bound
- * stated by the tests: 2e-4).
+ * The correlation with the segment transforms on the tensor cores (a reduced-precision variant;
+ * the paper has no counterpart): for segment length 2048 only, each forward (Eq. 3 sign) and
+ * inverse segment FFT is a 64-point DFT, a twist and a 32-point DFT done as DFT-matrix
+ * contractions (tcgen05 MMAs) with BF16 (precision FDAS_TC_BF16) or FP16 (FDAS_TC_FP16) operands
+ * split into hi + lo parts and FP32 accumulation; the DFT matrices are built in FP64 on the GPU.
+ * Same inputs, outputs and error codes as fdas_convolve_power (FDAS_ERR_INVALID also for
+ * seg_len != 2048 or another precision).  The first call on a plan (and the first after
+ * fdas_templates_build) allocates and fills a workspace of Z*L*8 + nseg*L*8 + 320 KB bytes; later
+ * calls allocate nothing.  Two kernel launches on `stream` (forward transforms into the
+ * workspace, then the correlation).  Per-row error against the FP64 definition is a few 1e-6 of
+ * the row peak (bound stated by the tests: 2e-4).
  */
 #define FDAS_TC_BF16 0
 #define FDAS_TC_FP16 1
 int fdas_convolve_power_tc(fdas_plan* plan, const float* d_spectrum, float* d_plane, int precision,
                            fdas_stream_t stream);
+
+/*
+ * The forward segment transforms of fdas_convolve_power_tc alone, for tests: d_out (nseg x L
+ * complex64, natural order, 16-byte aligned) receives X_s[k] = sum_j A[s V - h + j]
+ * exp(-2 pi i j k / L) (A = 0 outside [0, n)), as fdas_segment_spectra but on the tensor cores.
+ * Same errors and first-call allocation as fdas_convolve_power_tc; one launch on `stream`.
+ */
+int fdas_segment_spectra_tc(fdas_plan* plan, const float* d_spectrum, float* d_out, int precision,
+                            fdas_stream_t stream);
 
 /*
  * Synchronise `stream` and report the plan's device status word: FDAS_OK, FDAS_ERR_TIMEOUT

@@ -444,46 +444,82 @@ int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fd
   return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
-int fdas_convolve_power_tc(fdas_plan* p, const float* d_spectrum, float* d_plane, int precision,
-                           fdas_stream_t stream) {
-  if (!p || !d_spectrum || !d_plane || (precision != FDAS_TC_BF16 && precision != FDAS_TC_FP16))
-    return FDAS_ERR_INVALID;
-  if (!p->built) return FDAS_ERR_NOT_BUILT;
-  if (p->L != 2048) return FDAS_ERR_INVALID;
-  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u))
-    return FDAS_ERR_ALIGN;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!p->tc_ready) {
+namespace {
+
+// The tensor-core variant's workspace, allocated and filled on the first call after a template
+// build: natural-order bank, its max |Re|, |Im|, the four sets of DFT matrices, the segment
+// spectra.
+int tc_ensure_ready(fdas_plan* p, cudaStream_t st) {
+  if (p->tc_ready) return FDAS_OK;
+  free_tc_memory(p);
+  const int mb = fdas::tc_matrices_bytes();
+  if (cudaMalloc(&p->tc_bank, sizeof(float2) * (size_t)p->Z * p->L) != cudaSuccess ||
+      cudaMalloc(&p->tc_seg, sizeof(float2) * (size_t)p->nseg * p->L) != cudaSuccess ||
+      cudaMalloc(&p->tc_mats, 4 * (size_t)mb) != cudaSuccess ||
+      cudaMalloc(&p->tc_tmax, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
     free_tc_memory(p);
-    const int mb = fdas::tc_matrices_bytes();
-    if (cudaMalloc(&p->tc_bank, sizeof(float2) * (size_t)p->Z * p->L) != cudaSuccess ||
-        cudaMalloc(&p->tc_seg, sizeof(float2) * (size_t)p->nseg * p->L) != cudaSuccess ||
-        cudaMalloc(&p->tc_mats, 2 * (size_t)mb) != cudaSuccess ||
-        cudaMalloc(&p->tc_tmax, sizeof(unsigned)) != cudaSuccess) {
-      cudaGetLastError();
-      free_tc_memory(p);
-      return FDAS_ERR_ALLOC;
-    }
-    if (fdas::launch_tc_prepare(p->d_templates, p->Z, p->tc_bank, p->tc_tmax, p->tc_mats, p->tc_mats + mb, st) !=
-        cudaSuccess)
-      return FDAS_ERR_CUDA;
-    p->tc_ready = true;
+    return FDAS_ERR_ALLOC;
   }
-  const int rc = fdas_segment_spectra(p, d_spectrum, reinterpret_cast<float*>(p->tc_seg), stream);
-  if (rc != FDAS_OK) return rc;
+  if (fdas::launch_tc_prepare(p->d_templates, p->Z, p->tc_bank, p->tc_tmax, p->tc_mats, st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  p->tc_ready = true;
+  return FDAS_OK;
+}
+
+fdas::TcParams tc_params(const fdas_plan* p, const float* d_spectrum, int precision, bool forward) {
+  const int mb = fdas::tc_matrices_bytes();
   fdas::TcParams q;
   q.seg = p->tc_seg;
+  q.seg_out = p->tc_seg;
+  q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
   q.bank = p->tc_bank;
   q.twist = p->d_twist;
-  q.mats = p->tc_mats + (precision == FDAS_TC_FP16 ? fdas::tc_matrices_bytes() : 0);
+  q.mats = p->tc_mats + (size_t)mb * ((forward ? 2 : 0) + (precision == FDAS_TC_FP16 ? 1 : 0));
   q.tmax = p->tc_tmax;
-  q.plane = d_plane;
+  q.plane = nullptr;
   q.status = p->d_status;
   q.n_bins = p->n_bins;
-  q.units = p->nseg * (int64_t)((p->Z + 3) / 4);
+  q.nseg = p->nseg;
+  q.units = forward ? (p->nseg + 3) / 4 : p->nseg * (int64_t)((p->Z + 3) / 4);
   q.Z = p->Z;
   q.V = p->V;
-  return fdas::launch_tc(q, precision, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  q.h = p->h;
+  return q;
+}
+
+int tc_validate(fdas_plan* p, const void* a, const void* b, int precision) {
+  if (!p || !a || !b || (precision != FDAS_TC_BF16 && precision != FDAS_TC_FP16)) return FDAS_ERR_INVALID;
+  if (!p->built) return FDAS_ERR_NOT_BUILT;
+  if (p->L != 2048) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(a) & 15u) || (reinterpret_cast<uintptr_t>(b) & 15u)) return FDAS_ERR_ALIGN;
+  return FDAS_OK;
+}
+
+}  // namespace
+
+int fdas_convolve_power_tc(fdas_plan* p, const float* d_spectrum, float* d_plane, int precision,
+                           fdas_stream_t stream) {
+  int rc = tc_validate(p, d_spectrum, d_plane, precision);
+  if (rc != FDAS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((rc = tc_ensure_ready(p, st)) != FDAS_OK) return rc;
+  if (fdas::launch_tc(tc_params(p, d_spectrum, precision, true), precision, true, p->sm_count, st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  fdas::TcParams q = tc_params(p, d_spectrum, precision, false);
+  q.plane = d_plane;
+  return fdas::launch_tc(q, precision, false, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_segment_spectra_tc(fdas_plan* p, const float* d_spectrum, float* d_out, int precision,
+                            fdas_stream_t stream) {
+  int rc = tc_validate(p, d_spectrum, d_out, precision);
+  if (rc != FDAS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((rc = tc_ensure_ready(p, st)) != FDAS_OK) return rc;
+  fdas::TcParams q = tc_params(p, d_spectrum, precision, true);
+  q.seg_out = reinterpret_cast<float2*>(d_out);
+  return fdas::launch_tc(q, precision, true, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 int fdas_check(fdas_plan* p, fdas_stream_t stream) {

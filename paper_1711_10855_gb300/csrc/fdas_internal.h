@@ -79,21 +79,27 @@ cudaError_t launch_segment_spectra(int L, const CUtensorMap* spec_map, const Seg
                                    int sm_count, cudaStream_t stream);
 // Tensor-core variant for L = 2048 (fdas_tc.cu): inverse transforms as DFT-matrix contractions.
 struct TcParams {
-  const float2* seg;        // nseg x 2048 forward segment spectra, natural order
+  const float2* seg;        // nseg x 2048 forward segment spectra, natural order (inverse pass)
+  float2* seg_out;          // the same, written by the forward pass
+  const float2* spectrum;   // n_bins complex64 (forward pass)
   const float2* bank;       // Z x 2048 template spectra, natural order
   const float2* twist;      // the plan's twist table (pair-major layout, N1 = 32)
-  const unsigned char* mats;  // DFT matrices of the precision, operand layout (hi, lo)
+  const unsigned char* mats;  // DFT matrices of the precision and direction, operand layout (hi, lo)
   const unsigned* tmax;     // bits of max |Re|, |Im| over the bank
   float* plane;
   int* status;
   int64_t n_bins;
-  int64_t units;            // nseg x ceil(Z / 4)
-  int Z, V;
+  int64_t nseg;
+  int64_t units;            // inverse: nseg x ceil(Z / 4); forward: ceil(nseg / 4)
+  int Z, V, h;
 };
+// Bytes of one set of DFT matrices; the workspace holds four sets: inverse BF16, inverse FP16,
+// forward BF16, forward FP16.
 int tc_matrices_bytes();
-cudaError_t launch_tc_prepare(const float2* bank, int Z, float2* nat, unsigned* tmax, unsigned char* mats_bf16,
-                              unsigned char* mats_fp16, cudaStream_t stream);
-cudaError_t launch_tc(const TcParams& p, int precision, int sm_count, cudaStream_t stream);
+cudaError_t launch_tc_prepare(const float2* bank, int Z, float2* nat, unsigned* tmax, unsigned char* mats,
+                              cudaStream_t stream);
+// forward = true: the segment transforms (spectrum -> seg_out); false: the correlation (seg -> plane).
+cudaError_t launch_tc(const TcParams& p, int precision, bool forward, int sm_count, cudaStream_t stream);
 
 // Segment lengths 4096 and 8192 (fdas_convolve_big.cu); no tensor map.
 cudaError_t launch_convolve_big(int L, const ConvParams& p, int sm_count, cudaStream_t stream);

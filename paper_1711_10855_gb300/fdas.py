@@ -33,7 +33,8 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_zband_create", "fdas_zband_param_count", "fdas_zband_set_params", "fdas_zband_get_params",
             "fdas_zband_get_adam", "fdas_zband_set_adam", "fdas_zband_train_step", "fdas_zband_gradients",
             "fdas_zband_predict", "fdas_zband_propose", "fdas_zband_check", "fdas_zband_spectrum_windows",
-            "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc"]
+            "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc",
+            "fdas_segment_spectra_tc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -107,6 +108,8 @@ def lib() -> ctypes.CDLL:
             L.fdas_zband_get_params.restype = i32
             L.fdas_convolve_power_tc.argtypes = [vp, vp, vp, i32, vp]
             L.fdas_convolve_power_tc.restype = i32
+            L.fdas_segment_spectra_tc.argtypes = [vp, vp, vp, i32, vp]
+            L.fdas_segment_spectra_tc.restype = i32
             L.fdas_zband_get_adam.argtypes = [vp, vp, vp, vp]
             L.fdas_zband_get_adam.restype = i32
             L.fdas_zband_set_adam.argtypes = [vp, vp, vp, i32]
@@ -197,6 +200,12 @@ class Plan:
         prec = {"bf16": 0, "fp16": 1}[precision]
         _check(lib().fdas_convolve_power_tc(self._h, _ptr(spectrum), _ptr(plane), prec, _stream(stream)),
                "fdas_convolve_power_tc")
+
+    def segment_spectra_tc(self, spectrum, out, precision: str = "bf16", stream=None):
+        """Async: the forward segment transforms of convolve_power_tc (tensor cores) into out."""
+        prec = {"bf16": 0, "fp16": 1}[precision]
+        _check(lib().fdas_segment_spectra_tc(self._h, _ptr(spectrum), _ptr(out), prec, _stream(stream)),
+               "fdas_segment_spectra_tc")
 
     def segment_spectra(self, spectrum, out, stream=None):
         _check(lib().fdas_segment_spectra(self._h, _ptr(spectrum), _ptr(out), _stream(stream)),

@@ -136,3 +136,4 @@ def test_null_and_invalid_zband_calls(lib):
     assert lib.fdas_plan_group_segments(None) == -1
     assert lib.fdas_convolve_power_units(None, None, None, None, 1, None) == -1
     assert lib.fdas_convolve_power_tc(None, None, None, 0, None) == -1
+    assert lib.fdas_segment_spectra_tc(None, None, None, 0, None) == -1

@@ -1,6 +1,7 @@
-"""The tensor-core variant of the correlation (inverse transforms as DFT-matrix contractions with
-hi + lo BF16 / FP16 operands) against the FP64 oracle at the variant's bound, 2e-4 of each row's
-peak, and against the FP32 path on the survey plane, with the injected chirps recovered."""
+"""The tensor-core variant of the correlation (forward and inverse segment transforms as
+DFT-matrix contractions with hi + lo BF16 / FP16 operands) against the FP64 oracle at the
+variant's bound, 2e-4 of each row's peak, and against the FP32 path on the survey plane, with the
+injected chirps recovered."""
 import numpy as np
 import pytest
 
@@ -52,6 +53,40 @@ def test_tc_plane_matches_oracle(dev, precision, n, zmax, m):
     ref = oracle.plane_rows(spec, zmax, 2, m)
     worst = _rows_close(got, ref, TC_TOL)
     print(f"tc {precision} n={n}: worst row-relative error {worst:.2e}")
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("n,m", [(20000, 512), (9000, 64), (1536 * 5, 512)])
+def test_tc_segment_spectra_match_oracle(dev, precision, n, m):
+    """The forward transforms alone: every segment within 2e-5 of its peak |X_s| (first and last
+    segments zero-filled, a partial last unit of segments)."""
+    import torch
+    from paper_1711_10855_gb300 import fdas
+    spec = synth.noise_spectrum(n, seed=n + 3 * m)
+    ref = oracle.segment_spectra(spec, 2048, m)
+    with fdas.Plan(n, 4, 2, 2048, m) as plan:
+        plan.build_templates()
+        d = torch.from_numpy(np.ascontiguousarray(spec).view(np.float32).copy()).to(dev)
+        out = torch.full((plan.n_seg, 2 * 2048), float("nan"), dtype=torch.float32, device=dev)
+        plan.segment_spectra_tc(d, out, precision)
+        plan.check()
+        got = out.cpu().numpy().astype(np.float64).view(np.complex128)
+    assert got.shape == ref.shape and np.all(np.isfinite(got))
+    err = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    print(f"tc forward {precision} n={n} m={m}: worst segment-relative error {err.max():.2e}")
+    assert np.all(err <= 2e-5), (float(err.max()), int(np.argmax(err)))
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1e6])
+def test_tc_fp16_scales_small_and_large_spectra(dev, scale):
+    """FP16 has 5 exponent bits: spectra scaled by 1e-6 and 1e6 keep the 2e-4 row bound (the
+    operands are scaled into [2^10, 2^11) and the outputs back)."""
+    n = 12000
+    spec = (synth.noise_spectrum(n, seed=77) * scale).astype(np.complex64)
+    got = _tc_plane(spec, 10, 2, 512, dev, "fp16")
+    ref = oracle.plane_rows(spec, 10, 2, 512)
+    worst = _rows_close(got, ref, TC_TOL)
+    print(f"tc fp16 scale {scale:g}: worst row-relative error {worst:.2e}")
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
