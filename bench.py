@@ -371,6 +371,23 @@ def run_zband(args):
         rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
         points.append({"threshold": thr, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
                        "units": int(n_units)})
+    # a denser check of recall: 2^22 bins with a chirp in every 16th block (SNR as in training)
+    rng = np.random.default_rng(171110859)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(171110859)
+    chirps = zb.chirp_blocks(rng, 1, w.n_bins, w.zmax, tuple(args.zband_snr), every=16, snr_dist=args.zband_snr_dist)
+    spec2 = zb.chirp_spectra(torch, w.n_bins, chirps, gen, dev)[0]
+    plan.convolve_power(spec2, full)
+    plan.check()
+    dense_points = []
+    for t in args.zband_thresholds:
+        part.fill_(float("nan"))
+        n_units = ps.search(spec2, part, t)
+        plan.check()
+        rec, n_det, _, _ = zb.recall(torch, full, part, spec2, w.n_bins)
+        dense_points.append({"threshold": t, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
+                             "units": int(n_units)})
+    del spec2
     thr = args.zband_thresholds[0]
     for _ in range(args.warmup):
         ps.search(spec, part, thr)
@@ -406,6 +423,9 @@ def run_zband(args):
         "recall": points[0]["recall"], "unit_fraction": points[0]["unit_fraction"],
         "full_search_ms": full_ms, "full_search_cells_per_s": cells / (full_ms * 1e-3),
         "propose_ms": propose_ms, "operating_points": points,
+        "dense_operating_points": {"spectrum": f"2^22 bins, {int(chirps["z"].shape[1])} chirps (one per 16 blocks), "
+                                               f"SNR {args.zband_snr[0]:g}-{args.zband_snr[1]:g} {args.zband_snr_dist}",
+                                   "points": dense_points},
         "roofline": {"bound": "tensor", "kernel": "propose_kernel (+ median selection in the timed call)",
                      "achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                      "frac": tflops / float(peaks["bf16_tflops"]),
@@ -693,7 +713,7 @@ def main():
     ap.add_argument("--zband-snr", type=float, nargs=2, default=[5.0, 30.0])
     ap.add_argument("--zband-snr-dist", choices=["uniform", "log-uniform"], default="uniform")
     ap.add_argument("--zband-steps", type=int, default=8000)
-    ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.05, 0.08, 0.1])
+    ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.2, 0.05, 0.1, 0.3, 0.5])
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

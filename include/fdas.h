@@ -261,7 +261,9 @@ int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d
  *   x_r    = min(|A_r|^2 * ln 2 / med, 64)   med: lower median (rank (n-1)/2) of |A|^2 over the
  *            whole spectrum, so white-noise bins have mean 1 whatever the signals (x = 0 if med = 0)
  *   window w of width W (hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
- *   three k = 9 convolutions, 32 channels, zero padding 4 at the window edge, ReLU;
+ *   three k = 9 convolutions with dilations 1, 4, 16 (tap k of a layer with dilation d reads
+ *   position t + (k - 4) d), 32 channels, zero padding at the window edge, ReLU: a layer-3
+ *   position sees +-84 bins;
  *   the maximum of each channel over the central half [W/4, 3W/4) (= block [w*H, (w+1)*H));
  *   a linear layer to Z logits; training loss: mean BCE-with-logits against 0/1 targets.
  *
@@ -273,8 +275,8 @@ int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d
  * ------------------------------------------------------------------------------------------- */
 typedef struct fdas_zband fdas_zband;
 
-/* window W: a multiple of 128 in [128, 65536]; n_out = Z in [1, 65535]; max_batch windows per
- * call in [1, 65535].  Requires a compute capability 10.3 device (current device).  NULL on
+/* window W: a multiple of 128 in [384, 65536] (the receptive field, +-84, must fit in a quarter
+ * window); n_out = Z in [1, 65535]; max_batch windows per call in [1, 65535].  Requires a compute capability 10.3 device (current device).  NULL on
  * invalid arguments, another device, or allocation failure.  Parameters start at zero: set
  * them before use.  Device memory ~ 5 * max_batch * 32 * W floats. */
 fdas_zband* fdas_zband_create(int window, int n_out, int max_batch);
@@ -303,7 +305,7 @@ int fdas_zband_predict(fdas_zband* net, const float* d_windows, int batch, int h
  * complex64 (device, 8-byte aligned), d_logits ceil(n_bins / H) x Z floats (device).  Row w is
  * the network's output for window w (the same value fdas_zband_predict gives for that window,
  * up to FP16 rounding of the activations).  Requires H = W/2 to be a multiple of 128 and at
- * most 512.  Asynchronous, no allocation; uses the net's scratch, so calls on one net must not
+ * most 512 (W = 512, 768 or 1024).  Asynchronous, no allocation; uses the net's scratch, so calls on one net must not
  * overlap.  A bounded device wait that gives up is reported by fdas_zband_check. */
 int fdas_zband_propose(fdas_zband* net, const float* d_spectrum, int64_t n_bins, float* d_logits,
                        fdas_stream_t stream);

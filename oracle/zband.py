@@ -8,18 +8,20 @@ is the plain definition the CUDA kernels are checked against.
     x_r    = min(|A_r|^2 * ln 2 / med, X_CAP)     med = lower median of |A_r'|^2 over the
                                                    whole spectrum (noise: E x = 1), cap 64
     window w (width W, hop H = W/2): x over bins [w*H - W/4, w*H + 3W/4), 0 outside [0, n)
-    h1     = relu(conv_k9(x;  W1 (32,1,9),  b1))        zero padding 4 ("same") at the window edge
-    h2     = relu(conv_k9(h1; W2 (32,32,9), b2))
-    h3     = relu(conv_k9(h2; W3 (32,32,9), b3))
+    h1     = relu(conv_k9(x;  W1 (32,1,9),  b1; d = 1))   zero padding 4d ("same") at the window edge
+    h2     = relu(conv_k9(h1; W2 (32,32,9), b2; d = 4))
+    h3     = relu(conv_k9(h2; W3 (32,32,9), b3; d = 16))
     m[b,c] = max over the central positions [W/4, 3W/4) of h3[b,c,:]   (= bins of block w)
     logits = m @ Wl.T + bl                                (Wl: (Z, 32))
     loss   = mean over (b, j) of BCE-with-logits(logits, target)
 
-conv_k9(x; W, b)[b, o, t] = b[o] + sum_{i,k} W[o, i, k] * x[b, i, t + k - 4].
+conv_k9(x; W, b; d)[b, o, t] = b[o] + sum_{i,k} W[o, i, k] * x[b, i, t + (k - 4) d]  (dilation d).
 
-The central positions' receptive field (+-12 bins) stays inside the window, so the logits of
-block w equal those of the same layers run over the whole zero-extended x sequence and pooled
-over [w*H, (w+1)*H) -- the form the fast inference kernel computes.
+The dilations 1, 4, 16 give the central positions a receptive field of 4 (1 + 4 + 16) = +-84
+bins -- a chirp with fdot z spreads its z = 0 power over about |z| bins -- which stays inside
+the window when W >= 4 * 84, so the logits of block w equal those of the same layers run over
+the whole zero-extended x sequence and pooled over [w*H, (w+1)*H) -- the form the fast
+inference kernel computes.
 
 Only tests/ import this module.  The GPU implementation (csrc/fdas_zband.cu) shares nothing with it.
 Pins: tests/test_oracle_zband.py (direct sums, finite differences, closed forms of Adam's first
@@ -31,30 +33,34 @@ import numpy as np
 
 K = 9
 PAD = 4
+DIL = (1, 4, 16)                      # dilation of layers 1, 2, 3
+RF = PAD * sum(DIL)                   # receptive field of a layer-3 position: +-84 bins
 
 
-def conv_k9(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """(B, I, T) x (O, I, 9) -> (B, O, T), zero padding 4, FP64."""
+def conv_k9(x: np.ndarray, w: np.ndarray, b: np.ndarray, d: int = 1) -> np.ndarray:
+    """(B, I, T) x (O, I, 9) -> (B, O, T), dilation d, zero padding 4d, FP64."""
     B, I, T = x.shape
-    xp = np.zeros((B, I, T + 2 * PAD))
-    xp[:, :, PAD:PAD + T] = x
+    P = PAD * d
+    xp = np.zeros((B, I, T + 2 * P))
+    xp[:, :, P:P + T] = x
     out = np.zeros((B, w.shape[0], T))
     for k in range(K):
-        out += np.einsum("oi,bit->bot", w[:, :, k], xp[:, :, k:k + T])
+        out += np.einsum("oi,bit->bot", w[:, :, k], xp[:, :, k * d:k * d + T])
     return out + b[None, :, None]
 
 
-def conv_k9_backward(x, w, dout):
-    """Gradients of conv_k9 w.r.t. input, weights and bias."""
+def conv_k9_backward(x, w, dout, d: int = 1):
+    """Gradients of conv_k9 (dilation d) w.r.t. input, weights and bias."""
     B, I, T = x.shape
-    xp = np.zeros((B, I, T + 2 * PAD))
-    xp[:, :, PAD:PAD + T] = x
+    P = PAD * d
+    xp = np.zeros((B, I, T + 2 * P))
+    xp[:, :, P:P + T] = x
     dxp = np.zeros_like(xp)
     dw = np.zeros_like(w)
     for k in range(K):
-        dw[:, :, k] = np.einsum("bot,bit->oi", dout, xp[:, :, k:k + T])
-        dxp[:, :, k:k + T] += np.einsum("oi,bot->bit", w[:, :, k], dout)
-    return dxp[:, :, PAD:PAD + T], dw, dout.sum(axis=(0, 2))
+        dw[:, :, k] = np.einsum("bot,bit->oi", dout, xp[:, :, k * d:k * d + T])
+        dxp[:, :, k * d:k * d + T] += np.einsum("oi,bot->bit", w[:, :, k], dout)
+    return dxp[:, :, P:P + T], dw, dout.sum(axis=(0, 2))
 
 
 X_CAP = 64.0
@@ -97,11 +103,11 @@ def block_logits(params: dict, spectrum: np.ndarray, window: int) -> np.ndarray:
 def forward(params: dict, x: np.ndarray, keep: bool = False):
     """params: W1,b1,W2,b2,W3,b3,Wl,bl (float arrays).  x: (B, W) normalised windows."""
     h0 = np.asarray(x, dtype=np.float64)[:, None, :]
-    a1 = conv_k9(h0, params["W1"], params["b1"])
+    a1 = conv_k9(h0, params["W1"], params["b1"], DIL[0])
     h1 = np.maximum(a1, 0.0)
-    a2 = conv_k9(h1, params["W2"], params["b2"])
+    a2 = conv_k9(h1, params["W2"], params["b2"], DIL[1])
     h2 = np.maximum(a2, 0.0)
-    a3 = conv_k9(h2, params["W3"], params["b3"])
+    a3 = conv_k9(h2, params["W3"], params["b3"], DIL[2])
     h3 = np.maximum(a3, 0.0)
     T = h3.shape[2]
     lo, hi = T // 4, 3 * T // 4
@@ -133,11 +139,11 @@ def loss_and_grads(params: dict, x: np.ndarray, target: np.ndarray):
     B, C, _ = dh3.shape
     dh3[np.arange(B)[:, None], np.arange(C)[None, :], c["arg"]] = dm
     da3 = dh3 * (c["a3"] > 0)
-    dh2, g["W3"], g["b3"] = conv_k9_backward(c["h2"], params["W3"], da3)
+    dh2, g["W3"], g["b3"] = conv_k9_backward(c["h2"], params["W3"], da3, DIL[2])
     da2 = dh2 * (c["a2"] > 0)
-    dh1, g["W2"], g["b2"] = conv_k9_backward(c["h1"], params["W2"], da2)
+    dh1, g["W2"], g["b2"] = conv_k9_backward(c["h1"], params["W2"], da2, DIL[1])
     da1 = dh1 * (c["a1"] > 0)
-    _, g["W1"], g["b1"] = conv_k9_backward(c["h0"], params["W1"], da1)
+    _, g["W1"], g["b1"] = conv_k9_backward(c["h0"], params["W1"], da1, DIL[0])
     return loss, g
 
 

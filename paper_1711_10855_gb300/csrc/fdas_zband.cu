@@ -6,15 +6,18 @@
 // kernel.  The paper has no counterpart; the full search stays the reference against which
 // recall is measured.
 //
-// Network (window width Wd, hop Wd/2, C = 32 channels, k = 9, zero padding 4):
+// Network (window width Wd, hop Wd/2, C = 32 channels, k = 9, dilations 1, 4, 16, zero padding
+// 4 x dilation):
 //   x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)   (one scale for the whole spectrum)
 //   window w = x over bins [w*hop - Wd/4, w*hop + 3Wd/4), 0 outside [0, n)
-//   a1 = conv(x; W1, b1), a2 = conv(relu(a1); W2, b2), a3 = conv(relu(a2); W3, b3)
+//   a1 = conv_1(x; W1, b1), a2 = conv_4(relu(a1); W2, b2), a3 = conv_16(relu(a2); W3, b3)
+//     conv_d(in; W, b)[o][t] = b[o] + sum_{i,k} W[o][i][k] in[i][t + (k - 4) d]
 //   m[c] = max over t in [Wd/4, 3Wd/4) of relu(a3[c][t]),   logits = Wl m + bl  (Z outputs)
 //   loss = mean BCE-with-logits(logits, target)
-// The central positions' receptive field (+-12) stays inside the window, so the logits of
-// window w are those of the layers run once over the zero-extended x and max-pooled over the
-// block [w*hop, (w+1)*hop): the inference kernel computes that form, without the overlap.
+// The central positions' receptive field (+-84 = 4 (1 + 4 + 16)) stays inside the window
+// (Wd >= 4 x 84), so the logits of window w are those of the layers run once over the
+// zero-extended x and max-pooled over the block [w*hop, (w+1)*hop): the inference kernel
+// computes that form, without the overlap.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -33,6 +36,8 @@ constexpr int kC = 32;          // channels
 constexpr int kK = 9;           // kernel taps
 constexpr int kPad = 4;
 constexpr int kTile = 128;      // positions per conv block
+constexpr int kDil1 = 1, kDil2 = 4, kDil3 = 16;    // layer dilations
+constexpr int kRF = kPad * (kDil1 + kDil2 + kDil3);   // receptive field of a layer-3 position
 
 // Flat parameter layout (floats).
 struct Layout {
@@ -130,23 +135,26 @@ __global__ void spectrum_windows_kernel(const float2* spec, int64_t n, const flo
   for (int t = threadIdx.x; t < Wd; t += blockDim.x) x[w * Wd + t] = power_x(spec, n, r0 + t, sc);
 }
 
-// pre[b][o][t] = bias[o] + sum_{i,k} W[o][i][k] * in(b, i, t + k - 4); in = x (CIN = 1) or
+// pre[b][o][t] = bias[o] + sum_{i,k} W[o][i][k] * in(b, i, t + (k - 4) D); in = x (CIN = 1) or
 // relu(prev pre-activation).  Block: 128 positions of one window, all 32 output channels;
 // thread (o = tid/8, t = tid%8 + 8j).
-template <int CIN>
-constexpr size_t conv_fwd_smem() { return sizeof(float) * ((size_t)CIN * (kTile + 2 * kPad) + (size_t)kC * CIN * kK); }
+template <int CIN, int D>
+constexpr size_t conv_fwd_smem() {
+  return sizeof(float) * ((size_t)CIN * (kTile + 2 * kPad * D) + (size_t)kC * CIN * kK);
+}
 
-template <int CIN, bool RELU_IN, typename WT>
+template <int CIN, bool RELU_IN, typename WT, int D>
 __global__ void __launch_bounds__(256) conv_fwd_kernel(const float* in, const WT* W, const WT* bias, float* pre,
                                                        int Wd) {
+  constexpr int S = kTile + 2 * kPad * D;   // staged positions: the tile and its halo
   extern __shared__ float dyn[];
-  float (*sIn)[kTile + 2 * kPad] = reinterpret_cast<float (*)[kTile + 2 * kPad]>(dyn);
-  float* sW = dyn + (size_t)CIN * (kTile + 2 * kPad);
+  float (*sIn)[S] = reinterpret_cast<float (*)[S]>(dyn);
+  float* sW = dyn + (size_t)CIN * S;
   const int b = blockIdx.y, t0 = blockIdx.x * kTile;
   for (int idx = threadIdx.x; idx < kC * CIN * kK; idx += blockDim.x) sW[idx] = to_f(W[idx]);
-  for (int idx = threadIdx.x; idx < CIN * (kTile + 2 * kPad); idx += blockDim.x) {
-    const int i = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
-    const int t = t0 + tt - kPad;
+  for (int idx = threadIdx.x; idx < CIN * S; idx += blockDim.x) {
+    const int i = idx / S, tt = idx % S;
+    const int t = t0 + tt - kPad * D;
     float v = (t >= 0 && t < Wd) ? in[((size_t)b * CIN + i) * Wd + t] : 0.f;
     if (RELU_IN) v = fmaxf(v, 0.f);
     sIn[i][tt] = v;
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(const float* in, const WT
     for (int k = 0; k < kK; ++k) {
       const float w = sW[(o * CIN + i) * kK + k];
 #pragma unroll
-      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sIn[i][tl + 8 * j + k], acc[j]);
+      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sIn[i][tl + 8 * j + k * D], acc[j]);
     }
   }
 #pragma unroll
@@ -245,19 +253,24 @@ __global__ void head_bwd_data_kernel(const float* dlog, const float* Wl, const i
   da3[at] = a3[at] > 0.f ? s : 0.f;
 }
 
-// dIn_pre[b][i][t] = (prev_pre > 0) * sum_{o,k} W[o][i][k] dOut[b][o][t - k + 4].
-constexpr size_t kBwdDataSmem = sizeof(float) * ((size_t)kC * (kTile + 2 * kPad) + (size_t)kC * kC * kK);
+// dIn_pre[b][i][t] = (prev_pre > 0) * sum_{o,k} W[o][i][k] dOut[b][o][t - (k - 4) D].
+template <int D>
+constexpr size_t bwd_data_smem() {
+  return sizeof(float) * ((size_t)kC * (kTile + 2 * kPad * D) + (size_t)kC * kC * kK);
+}
 
+template <int D>
 __global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* dout, const float* W, const float* prev_pre,
                                                             float* din, int Wd) {
+  constexpr int S = kTile + 2 * kPad * D;
   extern __shared__ float dyn[];
-  float (*sD)[kTile + 2 * kPad] = reinterpret_cast<float (*)[kTile + 2 * kPad]>(dyn);
-  float* sW = dyn + (size_t)kC * (kTile + 2 * kPad);
+  float (*sD)[S] = reinterpret_cast<float (*)[S]>(dyn);
+  float* sW = dyn + (size_t)kC * S;
   const int b = blockIdx.y, t0 = blockIdx.x * kTile;
   for (int idx = threadIdx.x; idx < kC * kC * kK; idx += blockDim.x) sW[idx] = W[idx];
-  for (int idx = threadIdx.x; idx < kC * (kTile + 2 * kPad); idx += blockDim.x) {
-    const int o = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
-    const int t = t0 + tt - kPad;
+  for (int idx = threadIdx.x; idx < kC * S; idx += blockDim.x) {
+    const int o = idx / S, tt = idx % S;
+    const int t = t0 + tt - kPad * D;
     sD[o][tt] = (t >= 0 && t < Wd) ? dout[((size_t)b * kC + o) * Wd + t] : 0.f;
   }
   __syncthreads();
@@ -269,9 +282,9 @@ __global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* dout, c
 #pragma unroll
     for (int k = 0; k < kK; ++k) {
       const float w = sW[(o * kC + i) * kK + k];
-      // dOut index t - k + 4 = (t0 + tl + 8j) - k + 4 -> tile offset tl + 8j - k + 8
+      // dOut index t - (k - 4) D = (t0 + tl + 8j) - (k - 4) D -> tile offset tl + 8j + (8 - k) D
 #pragma unroll
-      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sD[o][tl + 8 * j + 2 * kPad - k], acc[j]);
+      for (int j = 0; j < kTile / 8; ++j) acc[j] = fmaf(w, sD[o][tl + 8 * j + (2 * kPad - k) * D], acc[j]);
     }
   }
 #pragma unroll
@@ -281,17 +294,24 @@ __global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* dout, c
   }
 }
 
-// dW[o][i][k] += sum_{t in tile} in(b, i, t + k - 4) * dOut[b][o][t]; db[o] += sum dOut.
+// dW[o][i][k] += sum_{t in tile} in(b, i, t + (k - 4) D) * dOut[b][o][t]; db[o] += sum dOut.
 // Block (tile, b); thread handles (o = tid/8) and i in {tid%8, tid%8 + 8, ...}.
-template <int CIN, bool RELU_IN>
+template <int CIN, int D>
+constexpr size_t bwd_weight_smem() {
+  return sizeof(float) * ((size_t)CIN * (kTile + 2 * kPad * D) + (size_t)kC * kTile);
+}
+
+template <int CIN, bool RELU_IN, int D>
 __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, const float* dout, int Wd, float* dW,
                                                               float* db) {
-  __shared__ float sIn[CIN][kTile + 2 * kPad];
-  __shared__ float sD[kC][kTile];
+  constexpr int S = kTile + 2 * kPad * D;
+  extern __shared__ float dyn[];
+  float (*sIn)[S] = reinterpret_cast<float (*)[S]>(dyn);
+  float (*sD)[kTile] = reinterpret_cast<float (*)[kTile]>(dyn + (size_t)CIN * S);
   const int b = blockIdx.y, t0 = blockIdx.x * kTile;
-  for (int idx = threadIdx.x; idx < CIN * (kTile + 2 * kPad); idx += blockDim.x) {
-    const int i = idx / (kTile + 2 * kPad), tt = idx % (kTile + 2 * kPad);
-    const int t = t0 + tt - kPad;
+  for (int idx = threadIdx.x; idx < CIN * S; idx += blockDim.x) {
+    const int i = idx / S, tt = idx % S;
+    const int t = t0 + tt - kPad * D;
     float v = (t >= 0 && t < Wd) ? in[((size_t)b * CIN + i) * Wd + t] : 0.f;
     if (RELU_IN) v = fmaxf(v, 0.f);
     sIn[i][tt] = v;
@@ -309,7 +329,7 @@ __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, c
     for (int t = 0; t < kTile; ++t) {
       const float d = sD[o][t];
 #pragma unroll
-      for (int k = 0; k < kK; ++k) acc[k] = fmaf(sIn[i][t + k], d, acc[k]);
+      for (int k = 0; k < kK; ++k) acc[k] = fmaf(sIn[i][t + k * D], d, acc[k]);
     }
 #pragma unroll
     for (int k = 0; k < kK; ++k) atomicAdd(&dW[(o * CIN + i) * kK + k], acc[k]);
@@ -387,21 +407,22 @@ __global__ void write_units_kernel(const unsigned char* flags, const int64_t* of
 // two independent groups of 4 warps, each with its own activation slot, half of the TMEM
 // allocation, mbarrier and named barriers, so one group's MMAs overlap the other's epilogues.
 // Group g of CTA b walks blocks w = 2b + g, 2b + g + 2*gridDim.x, ...; block w owns output
-// positions [w*hop, (w+1)*hop) and recomputes the +-12-position halo its three layers need:
-//   x   at P0-12 + j, j < 128*T1 + 8     (prefetched into registers one block ahead)
-//   h1  at P0-8 + r,  r < 128*T2 + 8     (layer 1 as an im2col GEMM: K = 9 taps padded to 16)
-//   h2  at P0-4 + r,  r < hop + 8        (layer 2: T2 M-tiles of 128 positions)
+// positions [w*hop, (w+1)*hop) and recomputes the +-84-position halo its three layers need
+// (dilations 1, 4, 16):
+//   x   at P0-84 + j, j < 128*T1 + 8     (prefetched into registers one block ahead)
+//   h1  at P0-80 + r, r < 128*T2 + 32    (layer 1 as an im2col GEMM: K = 9 taps padded to 16)
+//   h2  at P0-64 + r, r < hop + 128      (layer 2: T2 = T3 + 1 M-tiles of 128 positions)
 //   h3  at P0 + r,    r < hop            (layer 3: T3 = hop/128 M-tiles), max-pooled per channel
 // Activations sit in shared memory "chunk-planar": channel chunk j (8 channels, 16 B) of
 // position row r at plane j, offset 16*r.  A K-major no-swizzle operand whose rows are
-// positions is then one descriptor per (tap k, K-half c): start row + k, LBO = plane size,
-// SBO = 128 B -- the im2col of a k = 9 convolution costs no copies.
+// positions is then one descriptor per (tap k, K-half c): start row + k d, LBO = plane size,
+// SBO = 128 B -- the im2col of a dilated k = 9 convolution costs no copies.
 // ---------------------------------------------------------------------------------------
 constexpr int kMaxHop = 512;
 constexpr int kT3max = kMaxHop / 128;
 constexpr int kT2max = kT3max + 1;
 constexpr int kT1max = kT2max + 1;
-constexpr int kNP1 = 128 * kT2max + 8;          // h1 rows (plane height)
+constexpr int kNP1 = 128 * kT2max + 8 * kDil2;  // h1 rows (plane height)
 constexpr int kNP2 = 128 * kT2max;              // h2 rows (plane height)
 constexpr int kNA1 = 128 * kT1max;              // im2col rows of layer 1
 constexpr int kNX = kNA1 + 8;                   // staged x values
@@ -425,6 +446,8 @@ constexpr int kOffTslot = kOffGroup + 2 * kGroupMisc;
 constexpr int kProposeSmem = kOffTslot + 16;
 constexpr uint32_t kIdesc = fdas::umma_idesc_f16(128, kC);
 constexpr uint32_t kTmemCols = 512;             // 256 columns per group (<= 6 x 32 used)
+static_assert(kDil1 == 1, "layer 1 is an im2col of adjacent x values");
+static_assert(8 * kDil3 <= 128 && 8 * kDil2 <= 128, "each layer's halo fits in one extra 128-row tile");
 static_assert(2 * kPlaneA1 <= 4 * kPlaneH2, "im2col must fit in the h2 planes");
 static_assert(kNX * 4 <= (int)(4 * kPlaneH1), "staged x must fit in the h1 planes");
 static_assert(32 * kT1max <= (int)kTmemCols / 2, "accumulators must fit a group's TMEM half");
@@ -530,7 +553,7 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
 #pragma unroll
     for (int e = 0; e < kXPer; ++e) {
       const int j = gt + kGroupThreads * e;
-      const int64_t r = P0 - 12 + j;
+      const int64_t r = P0 - kRF + j;
       xa[e] = (j < nx && r >= 0 && r < p.n) ? __ldg(p.spec + r) : make_float2(0.f, 0.f);
     }
   };
@@ -579,18 +602,19 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       }
     });
   };
-  // one k = 9 convolution layer: NT M-tiles, A rows start at 128t + k in the source planes;
-  // tiles innermost, so consecutive MMAs feed independent accumulators.  A descriptor's start
-  // address is its low field, so every operand is a base descriptor plus a constant.
-  auto issue_conv = [&](auto ntiles, uint32_t src, uint32_t plane, uint32_t wts) {
-    constexpr int NT = decltype(ntiles)::value;
+  // one k = 9 convolution layer with dilation D: NT M-tiles, A rows start at 128t + kD in the
+  // source planes; tiles innermost, so consecutive MMAs feed independent accumulators.  A
+  // descriptor's start address is its low field, so every operand is a base descriptor plus a
+  // constant.
+  auto issue_conv = [&](auto ntiles, auto dil, uint32_t src, uint32_t plane, uint32_t wts) {
+    constexpr int NT = decltype(ntiles)::value, D = decltype(dil)::value;
     const uint64_t a0 = umma_desc(src, plane, 128), b0 = umma_desc(wts, 512, 128);
     static_for<kK>([&](auto kk) {
       constexpr int k = decltype(kk)::value;
       static_for<2>([&](auto cc) {
         constexpr int c = decltype(cc)::value;
         const uint64_t bd = b0 + (uint64_t)((k * 2048 + c * 1024) >> 4);
-        const uint64_t ac = a0 + (uint64_t)(((uint32_t)k * 16 + 2u * c * plane) >> 4);
+        const uint64_t ac = a0 + (uint64_t)(((uint32_t)(k * D) * 16 + 2u * c * plane) >> 4);
         static_for<NT>([&](auto tt) {
           constexpr int t = decltype(tt)::value;
           umma_f16(tm + 32 * t, ac + (uint64_t)(128 * t), bd, kIdesc, (k | c) != 0);
@@ -612,7 +636,7 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     if (gt < kC) sMax[gt] = 0u;
     group_sync(g);
     if (w + wstep < p.n_blocks) load_x((w + wstep) * HOP);   // next block, used next iteration
-    // layer-1 im2col: row r (position P0-8+r) = x[r .. r+8], zero for K in [9, 16)
+    // layer-1 im2col: row r (position P0-80+r) = x[r .. r+8], zero for K in [9, 16)
     for (int r = gt; r < 128 * T1; r += kGroupThreads) {
       __half2 h[8];
 #pragma unroll
@@ -632,13 +656,13 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-    store_layer(std::integral_constant<int, T1>{}, 128 * T2 + 8, sBias, sH1, kPlaneH1);
+    store_layer(std::integral_constant<int, T1>{}, 128 * T2 + 8 * kDil2, sBias, sH1, kPlaneH1);
     sync_for_mma();
-    if (gt == 0) issue_conv(std::integral_constant<int, T2>{}, aH1, kPlaneH1, aW2);
+    if (gt == 0) issue_conv(std::integral_constant<int, T2>{}, std::integral_constant<int, kDil2>{}, aH1, kPlaneH1, aW2);
     if (!(ok = wait_mma())) break;
-    store_layer(std::integral_constant<int, T2>{}, HOP + 8, sBias + kC, sH2, kPlaneH2);
+    store_layer(std::integral_constant<int, T2>{}, HOP + 8 * kDil3, sBias + kC, sH2, kPlaneH2);
     sync_for_mma();
-    if (gt == 0) issue_conv(std::integral_constant<int, T3>{}, aH2, kPlaneH2, aW3);
+    if (gt == 0) issue_conv(std::integral_constant<int, T3>{}, std::integral_constant<int, kDil3>{}, aH2, kPlaneH2, aW3);
     if (!(ok = wait_mma())) break;
     // layer 3: relu(acc + b3), channel maxima over the block: each thread keeps the maximum of
     // its rows, then one warp reduction per channel (non-negative floats order as unsigned)
@@ -739,15 +763,21 @@ cudaError_t forward(fdas_zband* z, const float* in, int B, bool half_weights, cu
   const dim3 grid(z->Wd / kTile, B);
   if (half_weights) {
     const __half* h = z->ph;
-    conv_fwd_kernel<1, false, __half><<<grid, 256, conv_fwd_smem<1>(), st>>>(in, h + L.W1, h + L.b1, z->a1, z->Wd);
-    conv_fwd_kernel<kC, true, __half><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a1, h + L.W2, h + L.b2, z->a2, z->Wd);
-    conv_fwd_kernel<kC, true, __half><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a2, h + L.W3, h + L.b3, z->a3, z->Wd);
+    conv_fwd_kernel<1, false, __half, kDil1>
+        <<<grid, 256, conv_fwd_smem<1, kDil1>(), st>>>(in, h + L.W1, h + L.b1, z->a1, z->Wd);
+    conv_fwd_kernel<kC, true, __half, kDil2>
+        <<<grid, 256, conv_fwd_smem<kC, kDil2>(), st>>>(z->a1, h + L.W2, h + L.b2, z->a2, z->Wd);
+    conv_fwd_kernel<kC, true, __half, kDil3>
+        <<<grid, 256, conv_fwd_smem<kC, kDil3>(), st>>>(z->a2, h + L.W3, h + L.b3, z->a3, z->Wd);
     pool_head_kernel<__half><<<B, 256, 0, st>>>(z->a3, h + L.Wl, h + L.bl, z->Wd, z->Z, z->pooled, z->arg, z->logits);
   } else {
     const float* p = z->p;
-    conv_fwd_kernel<1, false, float><<<grid, 256, conv_fwd_smem<1>(), st>>>(in, p + L.W1, p + L.b1, z->a1, z->Wd);
-    conv_fwd_kernel<kC, true, float><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a1, p + L.W2, p + L.b2, z->a2, z->Wd);
-    conv_fwd_kernel<kC, true, float><<<grid, 256, conv_fwd_smem<kC>(), st>>>(z->a2, p + L.W3, p + L.b3, z->a3, z->Wd);
+    conv_fwd_kernel<1, false, float, kDil1>
+        <<<grid, 256, conv_fwd_smem<1, kDil1>(), st>>>(in, p + L.W1, p + L.b1, z->a1, z->Wd);
+    conv_fwd_kernel<kC, true, float, kDil2>
+        <<<grid, 256, conv_fwd_smem<kC, kDil2>(), st>>>(z->a1, p + L.W2, p + L.b2, z->a2, z->Wd);
+    conv_fwd_kernel<kC, true, float, kDil3>
+        <<<grid, 256, conv_fwd_smem<kC, kDil3>(), st>>>(z->a2, p + L.W3, p + L.b3, z->a3, z->Wd);
     pool_head_kernel<float><<<B, 256, 0, st>>>(z->a3, p + L.Wl, p + L.bl, z->Wd, z->Z, z->pooled, z->arg, z->logits);
   }
   return cudaGetLastError();
@@ -768,8 +798,10 @@ void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* 
 extern "C" {
 
 fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
-  if (window < kTile || window % kTile != 0 || window > (1 << 16) || n_out < 1 || n_out > 65535 || max_batch < 1 ||
-      max_batch > 65535)
+  // the window's quarter margins must hold the receptive field (the windowed and whole-sequence
+  // forms then agree)
+  if (window < 4 * kRF || window % kTile != 0 || window > (1 << 16) || n_out < 1 || n_out > 65535 ||
+      max_batch < 1 || max_batch > 65535)
     return nullptr;
   int dev = 0, major = 0, minor = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) ||
@@ -778,13 +810,20 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
     cudaGetLastError();
     return nullptr;
   }
-  if (cudaFuncSetAttribute(conv_fwd_kernel<kC, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_fwd_smem<kC>()) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_fwd_kernel<kC, true, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_fwd_smem<kC>()) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_bwd_data_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdDataSmem) !=
+  constexpr auto kSmemAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (cudaFuncSetAttribute(conv_fwd_kernel<kC, true, float, kDil2>, kSmemAttr, (int)conv_fwd_smem<kC, kDil2>()) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(propose_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
+      cudaFuncSetAttribute(conv_fwd_kernel<kC, true, float, kDil3>, kSmemAttr, (int)conv_fwd_smem<kC, kDil3>()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(conv_fwd_kernel<kC, true, __half, kDil2>, kSmemAttr, (int)conv_fwd_smem<kC, kDil2>()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(conv_fwd_kernel<kC, true, __half, kDil3>, kSmemAttr, (int)conv_fwd_smem<kC, kDil3>()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(conv_bwd_data_kernel<kDil2>, kSmemAttr, (int)bwd_data_smem<kDil2>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_bwd_data_kernel<kDil3>, kSmemAttr, (int)bwd_data_smem<kDil3>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_bwd_weight_kernel<kC, true, kDil2>, kSmemAttr, (int)bwd_weight_smem<kC, kDil2>()) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(conv_bwd_weight_kernel<kC, true, kDil3>, kSmemAttr, (int)bwd_weight_smem<kC, kDil3>()) !=
           cudaSuccess ||
       cudaFuncSetAttribute(propose_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
           cudaSuccess ||
@@ -882,11 +921,14 @@ int fdas_zband_train_step(fdas_zband* z, const float* d_windows, const float* d_
   cudaMemsetAsync(z->d1, 0, act * 4, st);
   head_bwd_data_kernel<<<B, kC, 0, st>>>(z->dlog, z->p + L.Wl, z->arg, z->a3, Z, Wd, z->d1);   // da3
   const dim3 grid(Wd / kTile, B);
-  conv_bwd_weight_kernel<kC, true><<<grid, 256, 0, st>>>(z->a2, z->d1, Wd, z->g + L.W3, z->g + L.b3);
-  conv_bwd_data_kernel<<<grid, 256, kBwdDataSmem, st>>>(z->d1, z->p + L.W3, z->a2, z->d2, Wd);   // da2
-  conv_bwd_weight_kernel<kC, true><<<grid, 256, 0, st>>>(z->a1, z->d2, Wd, z->g + L.W2, z->g + L.b2);
-  conv_bwd_data_kernel<<<grid, 256, kBwdDataSmem, st>>>(z->d2, z->p + L.W2, z->a1, z->d1, Wd);   // da1
-  conv_bwd_weight_kernel<1, false><<<grid, 256, 0, st>>>(d_windows, z->d1, Wd, z->g + L.W1, z->g + L.b1);
+  conv_bwd_weight_kernel<kC, true, kDil3>
+      <<<grid, 256, bwd_weight_smem<kC, kDil3>(), st>>>(z->a2, z->d1, Wd, z->g + L.W3, z->g + L.b3);
+  conv_bwd_data_kernel<kDil3><<<grid, 256, bwd_data_smem<kDil3>(), st>>>(z->d1, z->p + L.W3, z->a2, z->d2, Wd);   // da2
+  conv_bwd_weight_kernel<kC, true, kDil2>
+      <<<grid, 256, bwd_weight_smem<kC, kDil2>(), st>>>(z->a1, z->d2, Wd, z->g + L.W2, z->g + L.b2);
+  conv_bwd_data_kernel<kDil2><<<grid, 256, bwd_data_smem<kDil2>(), st>>>(z->d2, z->p + L.W2, z->a1, z->d1, Wd);   // da1
+  conv_bwd_weight_kernel<1, false, kDil1>
+      <<<grid, 256, bwd_weight_smem<1, kDil1>(), st>>>(d_windows, z->d1, Wd, z->g + L.W1, z->g + L.b1);
   z->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)z->step), c2 = 1.f - powf(b2, (float)z->step);
@@ -954,7 +996,6 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
   const int64_t pairs = (nb + 1) / 2;
   const unsigned grid = (unsigned)(pairs < z->sm_count ? pairs : z->sm_count);
   switch (hop) {
-    case 128: propose_kernel<128><<<grid, 256, kProposeSmem, st>>>(q); break;
     case 256: propose_kernel<256><<<grid, 256, kProposeSmem, st>>>(q); break;
     case 384: propose_kernel<384><<<grid, 256, kProposeSmem, st>>>(q); break;
     default: propose_kernel<512><<<grid, 256, kProposeSmem, st>>>(q); break;

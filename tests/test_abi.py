@@ -117,8 +117,9 @@ def test_batch_create_validation_without_device(lib):
 def test_null_and_invalid_zband_calls(lib):
     """Host-side validation of the proposal network's calls (returns before any device work)."""
     lib.fdas_zband_create.restype = ctypes.c_void_p
-    for args in [(100, 201, 8), (1000, 201, 8), (1 << 17, 201, 8), (1024, 0, 8), (1024, 70000, 8),
-                 (1024, 201, 0), (1024, 201, 70000)]:
+    # windows below 4 x 84 (the receptive field in each quarter margin) are rejected: 256
+    for args in [(100, 201, 8), (1000, 201, 8), (256, 201, 8), (1 << 17, 201, 8), (1024, 0, 8),
+                 (1024, 70000, 8), (1024, 201, 0), (1024, 201, 70000)]:
         assert not lib.fdas_zband_create(*args), args
     assert lib.fdas_zband_param_count(None) == -1
     assert lib.fdas_zband_set_params(None, None) == -1

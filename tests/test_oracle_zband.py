@@ -6,7 +6,7 @@ import pytest
 from oracle import zband
 
 
-def _direct_conv(x, w, b):
+def _direct_conv(x, w, b, d):
     B, I, T = x.shape
     O = w.shape[0]
     out = np.zeros((B, O, T))
@@ -16,19 +16,35 @@ def _direct_conv(x, w, b):
                 s = b[o]
                 for i in range(I):
                     for k in range(9):
-                        tt = t + k - 4
+                        tt = t + (k - 4) * d
                         if 0 <= tt < T:
                             s += w[o, i, k] * x[bb, i, tt]
                 out[bb, o, t] = s
     return out
 
 
-def test_conv_matches_direct_sum():
-    rng = np.random.default_rng(0)
-    x = rng.standard_normal((2, 3, 17))
+@pytest.mark.parametrize("d", [1, 4, 16])
+def test_conv_matches_direct_sum(d):
+    rng = np.random.default_rng(d)
+    x = rng.standard_normal((2, 3, 70))
     w = rng.standard_normal((4, 3, 9))
     b = rng.standard_normal(4)
-    np.testing.assert_allclose(zband.conv_k9(x, w, b), _direct_conv(x, w, b), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(zband.conv_k9(x, w, b, d), _direct_conv(x, w, b, d), rtol=1e-13, atol=1e-13)
+
+
+def test_network_dilations_and_receptive_field():
+    """Layer dilations 1, 4, 16: an impulse in x reaches exactly the layer-3 positions within
+    +-84 of it (nonnegative weights and zero biases, so nothing cancels)."""
+    assert zband.DIL == (1, 4, 16) and zband.RF == 84
+    params = zband.init_params(n_out=2, seed=4, channels=3)
+    for k in ("W1", "W2", "W3"):
+        params[k] = np.abs(params[k]) + 0.1
+    T, c = 400, 200
+    x = np.zeros((1, T))
+    x[0, c] = 1.0
+    _, cache = zband.forward(params, x, keep=True)
+    reach = np.nonzero(cache["h3"][0].max(axis=0) > 0)[0]
+    assert reach.min() == c - 84 and reach.max() == c + 84 and reach.size == 169
 
 
 def test_gradients_match_finite_differences():
@@ -111,9 +127,9 @@ def test_windows_by_index_and_centre_halves_tile_the_spectrum():
 
 def test_block_logits_equal_the_whole_sequence_network():
     """The windowed definition equals the layers run once over the zero-extended sequence and
-    max-pooled per block (the receptive field of +-12 bins stays inside each window)."""
+    max-pooled per block (the receptive field of +-84 bins stays inside each window)."""
     rng = np.random.default_rng(5)
-    n, W = 200, 64
+    n, W = 1300, 512
     H = W // 2
     spec = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     params = zband.init_params(n_out=5, seed=6, channels=4)
@@ -121,13 +137,13 @@ def test_block_logits_equal_the_whole_sequence_network():
         params[k] = rng.standard_normal(params[k].shape) * 0.3    # nonzero biases: padding matters
     x = zband.power_x(spec)
     nb = zband.n_blocks(n, W)
-    E = 16                                  # zero extension on both sides (> 12)
+    E = 96                                  # zero extension on both sides (> 84)
     total = nb * H + 2 * E
     seq = np.zeros(total)
     seq[E:E + n] = x
     h = seq[None, None, :]
-    for wk, bk in (("W1", "b1"), ("W2", "b2"), ("W3", "b3")):
-        h = np.maximum(zband.conv_k9(h, params[wk], params[bk]), 0.0)
+    for (wk, bk), d in zip((("W1", "b1"), ("W2", "b2"), ("W3", "b3")), zband.DIL):
+        h = np.maximum(zband.conv_k9(h, params[wk], params[bk], d), 0.0)
     pooled = np.stack([h[0, :, E + w * H:E + (w + 1) * H].max(axis=1) for w in range(nb)])
     want = pooled @ params["Wl"].T + params["bl"]
     np.testing.assert_allclose(zband.block_logits(params, spec, W), want, rtol=1e-12, atol=1e-12)
