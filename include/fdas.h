@@ -322,10 +322,14 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
  * < 1) for template z in a block w whose bins [w*hop, (w+1)*hop) meet [g*group_bins - h,
  * (g+1)*group_bins + h) (group_bins = G*V: the outputs of segment group g and the input bins
  * its templates reach).  Writes the ascending list to d_units (room for n_groups*Z int32) and
- * its length to *host_count (synchronises `stream`).  Uses stream-ordered scratch. */
+ * its length to *host_count (synchronises `stream`).  d_scratch: device workspace of at least
+ * fdas_zband_work_units_scratch_bytes(n_groups, Z) bytes, 16-byte aligned, caller-owned, or
+ * NULL for stream-ordered allocations inside the call (which the memory pool may return to the
+ * system at the synchronisation, making every call map them again). */
+int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z);
 int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
-                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, int64_t* host_count,
-                          fdas_stream_t stream);
+                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,
+                          int64_t* host_count, fdas_stream_t stream);
 int fdas_zband_destroy(fdas_zband* net);
 
 /*

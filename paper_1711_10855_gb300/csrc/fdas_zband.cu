@@ -381,24 +381,67 @@ __global__ void group_flags_kernel(const float* logits, int n_win, int Z, float 
   if (threadIdx.x == 0) counts[g] = cnt;
 }
 
-// Exclusive scan of per-group counts (one block, sequential chunks) and the total.
-__global__ void scan_counts_kernel(const int* counts, int n_groups, int64_t* offsets, int64_t* total) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int64_t s = 0;
-  for (int g = 0; g < n_groups; ++g) {
-    offsets[g] = s;
-    s += counts[g];
+// Exclusive scan of per-group counts and the total: one block of 1024 threads, thread t owning
+// the contiguous chunk [t c, (t+1) c) of the groups; chunk sums are scanned with warp shuffles.
+__global__ void __launch_bounds__(1024) scan_counts_kernel(const int* counts, int n_groups, int64_t* offsets,
+                                                           int64_t* total) {
+  __shared__ int64_t warp_excl[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = (n_groups + 1023) / 1024;
+  const int b = tid * chunk < n_groups ? tid * chunk : n_groups;
+  const int e = b + chunk < n_groups ? b + chunk : n_groups;
+  int64_t own = 0;
+  for (int g = b; g < e; ++g) own += counts[g];
+  int64_t incl = own;   // inclusive scan over the warp
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
   }
-  *total = s;
+  if (lane == 31) warp_excl[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int64_t ws = warp_excl[lane];
+    int64_t wi = ws;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, wi, off);
+      if (lane >= off) wi += y;
+    }
+    warp_excl[lane] = wi - ws;
+  }
+  __syncthreads();
+  int64_t run = warp_excl[wid] + incl - own;
+  for (int g = b; g < e; ++g) {
+    offsets[g] = run;
+    run += counts[g];
+  }
+  if (tid == 1023) *total = run;
 }
 
-// units[offset_g + k] = g*Z + z for the k-th proposed z of group g (increasing z).
-__global__ void write_units_kernel(const unsigned char* flags, const int64_t* offsets, int Z, int32_t* units) {
-  const int g = blockIdx.x;
-  if (threadIdx.x != 0) return;
-  int64_t o = offsets[g];
-  for (int z = 0; z < Z; ++z)
-    if (flags[(size_t)g * Z + z]) units[o++] = (int32_t)((int64_t)g * Z + z);
+// units[offset_g + k] = g*Z + z for the k-th proposed z of group g (increasing z): one block of
+// 256 threads per group, each flag placed by the popcount of the flags before it.
+__global__ void __launch_bounds__(256) write_units_kernel(const unsigned char* flags, const int64_t* offsets, int Z,
+                                                          int32_t* units) {
+  __shared__ int warp_cnt[8];
+  const int g = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t base = offsets[g];
+  for (int z0 = 0; z0 < Z; z0 += 256) {
+    const int z = z0 + (int)threadIdx.x;
+    const bool f = z < Z && flags[(size_t)g * Z + z] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_cnt[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      before += i < wid ? warp_cnt[i] : 0;
+      all += warp_cnt[i];
+    }
+    if (f) units[base + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)((int64_t)g * Z + z);
+    base += all;
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1038,40 +1081,48 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
   return rc;
 }
 
+// Work-list scratch: offsets (int64, n_groups + 1), counts (int32, n_groups), flags (n_groups * Z
+// bytes), each 16-byte aligned.
+static int64_t align16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+static int64_t units_scratch_bytes(int64_t n_groups, int Z) {
+  return align16(8 * (n_groups + 1)) + align16(4 * n_groups) + align16(n_groups * (int64_t)Z);
+}
+
+int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z) {
+  if (n_groups < 1 || n_groups > (1 << 24) || Z < 1 || n_groups * (int64_t)Z > INT32_MAX) return FDAS_ERR_INVALID;
+  return units_scratch_bytes(n_groups, Z);
+}
+
 int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
-                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, int64_t* host_count,
-                          fdas_stream_t stream) {
+                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,
+                          int64_t* host_count, fdas_stream_t stream) {
   if (!d_logits || !d_units || !host_count || n_windows < 1 || n_windows > (1 << 30) || Z < 1 ||
       !(threshold > 0.f && threshold < 1.f) || hop < 1 || group_bins < 1 || h < 0 || n_groups < 1 ||
       n_groups > (1 << 24) || (int64_t)n_groups * Z > INT32_MAX)
     return FDAS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_scratch) & 15u) return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float logit_thr = logf(threshold / (1.f - threshold));
-  unsigned char* flags = nullptr;
-  int* counts = nullptr;
-  int64_t* offsets = nullptr;
-  if (cudaMallocAsync(&flags, (size_t)n_groups * Z, st) != cudaSuccess) return FDAS_ERR_ALLOC;
-  if (cudaMallocAsync(&counts, (size_t)n_groups * 4, st) != cudaSuccess) {
-    cudaFreeAsync(flags, st);
+  const int64_t bytes = units_scratch_bytes(n_groups, Z);
+  unsigned char* scratch = static_cast<unsigned char*>(d_scratch);
+  const bool own = scratch == nullptr;
+  if (own && cudaMallocAsync(reinterpret_cast<void**>(&scratch), (size_t)bytes, st) != cudaSuccess) {
+    cudaGetLastError();
     return FDAS_ERR_ALLOC;
   }
-  if (cudaMallocAsync(&offsets, (size_t)(n_groups + 1) * 8, st) != cudaSuccess) {
-    cudaFreeAsync(flags, st);
-    cudaFreeAsync(counts, st);
-    return FDAS_ERR_ALLOC;
-  }
+  int64_t* offsets = reinterpret_cast<int64_t*>(scratch);
+  int* counts = reinterpret_cast<int*>(scratch + align16(8 * (n_groups + 1)));
+  unsigned char* flags = scratch + align16(8 * (n_groups + 1)) + align16(4 * n_groups);
   group_flags_kernel<<<(unsigned)n_groups, 256, 0, st>>>(d_logits, (int)n_windows, Z, logit_thr, hop, group_bins, h,
                                                         (int)n_groups, flags, counts);
-  scan_counts_kernel<<<1, 32, 0, st>>>(counts, (int)n_groups, offsets, offsets + n_groups);
-  write_units_kernel<<<(unsigned)n_groups, 32, 0, st>>>(flags, offsets, Z, d_units);
+  scan_counts_kernel<<<1, 1024, 0, st>>>(counts, (int)n_groups, offsets, offsets + n_groups);
+  write_units_kernel<<<(unsigned)n_groups, 256, 0, st>>>(flags, offsets, Z, d_units);
   int rc = FDAS_OK;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(host_count, offsets + n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     rc = FDAS_ERR_CUDA;
-  cudaFreeAsync(flags, st);
-  cudaFreeAsync(counts, st);
-  cudaFreeAsync(offsets, st);
+  if (own) cudaFreeAsync(scratch, st);
   return rc;
 }
 

@@ -34,7 +34,7 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_zband_get_adam", "fdas_zband_set_adam", "fdas_zband_train_step", "fdas_zband_gradients",
             "fdas_zband_predict", "fdas_zband_propose", "fdas_zband_check", "fdas_zband_spectrum_windows",
             "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc",
-            "fdas_segment_spectra_tc"]
+            "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes"]
 
 _lock = threading.Lock()
 _lib = None
@@ -126,8 +126,10 @@ def lib() -> ctypes.CDLL:
             L.fdas_zband_predict.restype = i32
             L.fdas_zband_spectrum_windows.argtypes = [vp, i64, i32, i32, vp, i64, vp]
             L.fdas_zband_spectrum_windows.restype = i32
-            L.fdas_zband_work_units.argtypes = [vp, i64, i32, f32, i32, i64, i32, i64, vp, vp, vp]
+            L.fdas_zband_work_units.argtypes = [vp, i64, i32, f32, i32, i64, i32, i64, vp, vp, vp, vp]
             L.fdas_zband_work_units.restype = i32
+            L.fdas_zband_work_units_scratch_bytes.argtypes = [i64, i32]
+            L.fdas_zband_work_units_scratch_bytes.restype = i64
             L.fdas_zband_destroy.argtypes = [vp]
             L.fdas_zband_destroy.restype = i32
             L.fdas_selftest_wait_timeout.argtypes = [vp, i64, vp]
@@ -359,11 +361,22 @@ def zband_spectrum_windows(spectrum, n_bins: int, window: int, hop: int, windows
                                              int(n_windows), _stream(stream)), "fdas_zband_spectrum_windows")
 
 
+def zband_work_units_scratch_bytes(n_groups: int, n_z: int) -> int:
+    b = lib().fdas_zband_work_units_scratch_bytes(int(n_groups), int(n_z))
+    if b < 0:
+        raise FdasError(int(b), "fdas_zband_work_units_scratch_bytes")
+    return int(b)
+
+
 def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: int, group_bins: int, h: int,
-                     n_groups: int, units, stream=None) -> int:
+                     n_groups: int, units, stream=None, scratch=None) -> int:
+    """Async work list into `units`; returns its length (synchronises the stream).  `scratch`: a
+    device buffer of zband_work_units_scratch_bytes bytes reused across calls (None: allocated
+    inside the call)."""
     count = ctypes.c_int64(0)
     _check(lib().fdas_zband_work_units(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(hop),
-                                       int(group_bins), int(h), int(n_groups), _ptr(units), ctypes.byref(count),
+                                       int(group_bins), int(h), int(n_groups), _ptr(units),
+                                       None if scratch is None else _ptr(scratch), ctypes.byref(count),
                                        _stream(stream)), "fdas_zband_work_units")
     return count.value
 

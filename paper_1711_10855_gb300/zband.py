@@ -201,13 +201,15 @@ class ProposalSearch:
         self.n_groups = -(-plan.n_seg // self.G)
         self.logits = torch.empty((self.n_blocks, plan.n_z), dtype=torch.float32, device=dev)
         self.units = torch.empty(self.n_groups * plan.n_z, dtype=torch.int32, device=dev)
+        self.scratch = torch.empty(fdas.zband_work_units_scratch_bytes(self.n_groups, plan.n_z), dtype=torch.uint8,
+                                   device=dev)
         self.n_units = 0
 
     def propose(self, spectrum, threshold: float) -> int:
         self.net.propose(spectrum, self.plan.n_bins, self.logits)
         self.n_units = fdas.zband_work_units(self.logits, self.n_blocks, self.plan.n_z, threshold, HOP,
                                              self.G * self.plan.valid, self.plan.tmpl_len // 2, self.n_groups,
-                                             self.units)
+                                             self.units, scratch=self.scratch)
         return self.n_units
 
     def search(self, spectrum, plane, threshold: float) -> int:

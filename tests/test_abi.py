@@ -132,7 +132,12 @@ def test_null_and_invalid_zband_calls(lib):
     assert lib.fdas_zband_propose(None, None, 1024, None, None) == -1
     assert lib.fdas_zband_check(None, None) == -1
     assert lib.fdas_zband_spectrum_windows(None, 1024, 1024, 512, None, 3, None) == -1
-    assert lib.fdas_zband_work_units(None, 4, 201, ctypes.c_float(0.5), 512, 1536, 256, 2, None, None, None) == -1
+    assert lib.fdas_zband_work_units(None, 4, 201, ctypes.c_float(0.5), 512, 1536, 256, 2, None, None, None,
+                                     None) == -1
+    lib.fdas_zband_work_units_scratch_bytes.restype = ctypes.c_int64
+    lib.fdas_zband_work_units_scratch_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]
+    assert lib.fdas_zband_work_units_scratch_bytes(0, 201) == -1
+    assert lib.fdas_zband_work_units_scratch_bytes(342, 201) == 2752 + 1376 + 68752
     assert lib.fdas_zband_destroy(None) == 0
     assert lib.fdas_plan_group_segments(None) == -1
     assert lib.fdas_convolve_power_units(None, None, None, None, 1, None) == -1

@@ -180,17 +180,23 @@ def test_propose_large_spectrum_sampled_blocks_and_predict_agreement():
     assert np.abs(got - alt).max() <= 2e-2 * max(1.0, np.abs(alt).max())
 
 
-def test_work_units_match_oracle():
-    rng = np.random.default_rng(51)
-    nw, Z, thr = 37, 21, 0.3
+@pytest.mark.parametrize("nw,Z,G,n_groups,with_scratch", [(37, 21, 8, 2, False), (37, 21, 8, 2, True),
+                                                          (3000, 300, 8, 125, True), (3200, 5, 1, 1067, False)])
+def test_work_units_match_oracle(nw, Z, G, n_groups, with_scratch):
+    """Exact lists; Z = 300 spans two 256-template chunks of the writer, 1067 groups more than the
+    scan's 1024 threads; with a caller workspace and with per-call allocation."""
+    rng = np.random.default_rng(51 + nw)
+    thr = 0.3
     logits = rng.normal(-2.0, 2.0, (nw, Z)).astype(np.float32)
     lthr = np.log(thr / (1 - thr))
     near = np.abs(logits - lthr) < 1e-3
     logits[near] += 0.01
-    hop, V, G, h = 512, 1536, 8, 256
-    n_groups = 2
-    units = torch.empty(n_groups * Z, dtype=torch.int32, device="cuda")
-    n = fdas.zband_work_units(dev(logits), nw, Z, thr, hop, G * V, h, n_groups, units)
+    hop, V, h = 512, 1536, 256
+    units = torch.full((n_groups * Z,), -1, dtype=torch.int32, device="cuda")
+    scratch = None
+    if with_scratch:
+        scratch = torch.empty(fdas.zband_work_units_scratch_bytes(n_groups, Z), dtype=torch.uint8, device="cuda")
+    n = fdas.zband_work_units(dev(logits), nw, Z, thr, hop, G * V, h, n_groups, units, scratch=scratch)
     want = oz.work_units(logits.astype(np.float64), thr, hop, G * V, h, n_groups)
     assert n == want.size
     np.testing.assert_array_equal(units[:n].cpu().numpy(), want)
