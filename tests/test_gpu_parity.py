@@ -313,3 +313,46 @@ def test_bounded_wait_reports_timeout_and_context_survives(dev):
         plan.check()   # cleared
     got = gpu_plane(spec, 4, 2, 512, 64, dev)
     assert_rows_close(got, oracle.plane_rows(spec, 4, 2, 64))
+
+
+def test_maximum_spectrum_length_sampled(dev):
+    """n_bins = 2^30 (the largest the ABI accepts) with Z = 3: plane element indices reach
+    3.2e9 (row 2 lies wholly above 2^31).  Sampled cells of every row -- random bins, the last
+    segment seams, both spectrum edges -- against the oracle, for the FP32 path and the
+    tensor-core variant (BF16 hi + lo, 2e-4)."""
+    import torch
+    from paper_1711_10855_gb300 import fdas
+    n, zmax, zstep, L, m = 1 << 30, 2, 2, 2048, 512
+    g = torch.Generator(device=dev)
+    g.manual_seed(1711)
+    d_spec = torch.randn(2 * n, generator=g, device=dev, dtype=torch.float32)
+    spec = d_spec.cpu().numpy().view(np.complex64)
+    rng = np.random.default_rng(1712)
+    with fdas.Plan(n, zmax, zstep, L, m) as plan:
+        plan.build_templates()
+        Z, V, nseg = plan.n_z, plan.valid, plan.n_seg
+        zi, rr = [], []
+        for z in range(Z):
+            seam = np.arange(nseg - 3, nseg) * V
+            cells = np.r_[rng.integers(0, n, 48), seam - 1, seam, [0, 1, n - 2, n - 1]]
+            zi += [z] * cells.size
+            rr += list(cells)
+        zi, rr = np.array(zi), np.array(rr)
+        ref = oracle.plane_samples(spec, zmax, zstep, m, zi, rr)
+        plane = torch.empty((Z, n), dtype=torch.float32, device=dev)
+        ti, tr = torch.from_numpy(zi).to(dev), torch.from_numpy(rr).to(dev)
+        for run, tol in (("f32", ROW_TOL), ("bf16", 2e-4)):
+            plane.fill_(float("nan"))
+            if run == "f32":
+                plan.convolve_power(d_spec, plane)
+            else:
+                plan.convolve_power_tc(d_spec, plane, run)
+            plan.check()
+            got = plane[ti, tr].cpu().numpy().astype(np.float64)
+            for z in range(Z):
+                sel = zi == z
+                err = np.abs(got[sel] - ref[sel]).max() / ref[sel].max()
+                assert err <= tol, (run, z, err)
+        del plane
+    del d_spec
+    torch.cuda.empty_cache()
