@@ -147,3 +147,22 @@ def test_tc_rejects_other_segment_lengths_and_precisions(dev):
         assert e.value.code == fdas.FDAS_ERR_NOT_BUILT
         plan.build_templates()
         assert fdas.lib().fdas_convolve_power_tc(plan.handle, spec.data_ptr(), out.data_ptr(), 7, None) == -1
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("n", [4, 1532, 1540])
+def test_tc_tiny_spectra(dev, precision, n):
+    """One segment (n = 4, 1532 < V) and one bin past it (1540: two segments, 4 outputs in the
+    second), Z = 5: every cell against the oracle."""
+    spec = synth.noise_spectrum(n, seed=7 + n)
+    got = _tc_plane(spec, 4, 2, 512, dev, precision)
+    ref = oracle.plane_rows(spec, 4, 2, 512)
+    _rows_close(got, ref, TC_TOL)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tc_zero_spectrum_gives_zero_plane(dev, precision):
+    """All-zero input: the FP16 scale's bound is 0 (no scaling) and every cell is exactly 0."""
+    spec = np.zeros(5000, dtype=np.complex64)
+    got = _tc_plane(spec, 6, 2, 512, dev, precision)
+    assert np.all(got == 0.0)
