@@ -61,8 +61,11 @@ def workload(name: str, n_bins: int | None = None) -> synth.Workload:
     return w
 
 
-def algorithmic(w: synth.Workload, nseg: int) -> dict:
-    """Per-launch algorithmic bytes and flops of the correlation kernel."""
+def algorithmic(w: synth.Workload, nseg: int, group: int = 8) -> dict:
+    """Per-launch algorithmic bytes and flops of the correlation kernel, and the two co-limits:
+    shared-memory bytes (each inverse transform writes and reads its L points once in the
+    exchange and reads its template from the ring; each forward transform one exchange) and
+    L2-to-SM template bytes (each group of `group` segments streams the whole bank once)."""
     n, Z, L, m = w.n_bins, w.n_z, w.seg_len, w.tmpl_len
     V = L - m
     bytes_plane = 4 * Z * n
@@ -71,7 +74,10 @@ def algorithmic(w: synth.Workload, nseg: int) -> dict:
     logL = int(np.log2(L))
     fft = 5 * L * logL                 # nominal complex FFT flops
     flops = nseg * Z * (fft + 6 * L + 3 * V) + nseg * fft
-    return {"bytes": bytes_plane + bytes_spec + bytes_tmpl, "bytes_plane": bytes_plane, "flops": flops}
+    smem = nseg * Z * (2 * 8 * L + 8 * L) + nseg * 2 * 8 * L
+    l2_tmpl = -(-nseg // group) * Z * 8 * L
+    return {"bytes": bytes_plane + bytes_spec + bytes_tmpl, "bytes_plane": bytes_plane, "flops": flops,
+            "smem_bytes": smem, "l2_template_bytes": l2_tmpl}
 
 
 class ClockSampler:
@@ -553,7 +559,7 @@ def run_ours(args):
         return 0
 
     peaks, peak_src = measured_peaks()
-    alg = algorithmic(w, plan.n_seg)
+    alg = algorithmic(w, plan.n_seg, plan.group_segments if w.seg_len <= 2048 else 1)
     hbm_peak = float(peaks["hbm_gbs"])
     hbm_achieved = alg["bytes"] / (ms * 1e-3) / 1e9
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -583,6 +589,16 @@ def run_ours(args):
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": hbm_achieved / hbm_peak, "peak_source": f"hbm_gbs ({peak_src})",
                          "bytes_per_launch": alg["bytes"]},
+        "co_limits": {"note": "shared-memory Stockham kernel (L >= 4096): co-limits not modeled"}
+        if w.seg_len > 2048 else {
+            "smem_exchange": {"bytes_per_launch": alg["smem_bytes"],
+                              "achieved": alg["smem_bytes"] / (ms * 1e-3) / 1e9, "unit": "GB/s",
+                              "peak": SM_COUNT_GB300 * 128 * sm_max * 1e6 / 1e9,
+                              "frac": alg["smem_bytes"] / (ms * 1e-3) / (SM_COUNT_GB300 * 128 * sm_max * 1e6),
+                              "peak_source": f"152 SMs x 128 B/clock x {sm_max:.0f} MHz (nominal)"},
+            "l2_template_reads": {"bytes_per_launch": alg["l2_template_bytes"],
+                                  "achieved": alg["l2_template_bytes"] / (ms * 1e-3) / 1e9, "unit": "GB/s",
+                                  "peak": None, "peak_source": "no measured L2 peak"}},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(d_spec.numel() * 4),
                 "d2h_bytes_per_step": int(plane.numel() * 4), "steps": e2e_steps,

@@ -44,6 +44,11 @@ def test_algorithmic_counts_of_the_survey_plane():
     assert abs(a["bytes"] / 1e9 - 3.420) < 1e-3
     assert a["flops"] == 2731 * 201 * (5 * 2048 * 11 + 6 * 2048 + 3 * 1536) + 2731 * 5 * 2048 * 11
     assert abs(a["flops"] / 1e9 - 71.41) < 0.01
+    # co-limits: 3 x 16 KB of shared traffic per inverse transform, 2 x 16 KB per forward one;
+    # the 3.3 MB bank streamed once per group of 8 segments (342 groups)
+    assert a["smem_bytes"] == 2731 * 201 * 3 * 16384 + 2731 * 2 * 16384
+    assert a["l2_template_bytes"] == 342 * 201 * 16384
+    assert abs(a["l2_template_bytes"] / 1e9 - 1.126) < 1e-3
 
 
 def test_batch_workload_shape():
