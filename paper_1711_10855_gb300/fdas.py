@@ -140,6 +140,14 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
+def _tc_precision(precision: str) -> int:
+    """FDAS_TC_BF16 / FDAS_TC_FP16 for "bf16" / "fp16"."""
+    codes = {"bf16": 0, "fp16": 1}
+    if precision not in codes:
+        raise ValueError(f"precision must be 'bf16' or 'fp16', not {precision!r}")
+    return codes[precision]
+
+
 def error_string(code: int) -> str:
     return lib().fdas_error_string(int(code)).decode()
 
@@ -199,13 +207,13 @@ class Plan:
     def convolve_power_tc(self, spectrum, plane, precision: str = "bf16", stream=None):
         """Async: as convolve_power with the inverse transforms on the tensor cores (seg_len 2048;
         precision "bf16" or "fp16", operands split into hi + lo)."""
-        prec = {"bf16": 0, "fp16": 1}[precision]
+        prec = _tc_precision(precision)
         _check(lib().fdas_convolve_power_tc(self._h, _ptr(spectrum), _ptr(plane), prec, _stream(stream)),
                "fdas_convolve_power_tc")
 
     def segment_spectra_tc(self, spectrum, out, precision: str = "bf16", stream=None):
         """Async: the forward segment transforms of convolve_power_tc (tensor cores) into out."""
-        prec = {"bf16": 0, "fp16": 1}[precision]
+        prec = _tc_precision(precision)
         _check(lib().fdas_segment_spectra_tc(self._h, _ptr(spectrum), _ptr(out), prec, _stream(stream)),
                "fdas_segment_spectra_tc")
 

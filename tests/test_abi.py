@@ -143,3 +143,10 @@ def test_null_and_invalid_zband_calls(lib):
     assert lib.fdas_convolve_power_units(None, None, None, None, 1, None) == -1
     assert lib.fdas_convolve_power_tc(None, None, None, 0, None) == -1
     assert lib.fdas_segment_spectra_tc(None, None, None, 0, None) == -1
+
+
+def test_tc_precision_names():
+    from paper_1711_10855_gb300 import fdas
+    assert fdas._tc_precision("bf16") == 0 and fdas._tc_precision("fp16") == 1
+    with pytest.raises(ValueError):
+        fdas._tc_precision("fp8")
