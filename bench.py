@@ -414,6 +414,7 @@ def run_zband(args):
     step_ms = []
     torch.cuda.synchronize(dev)
     with ClockSampler(0) as clk:
+        time.sleep(0.3)   # a few clock samples before the short timed region
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize(dev)
