@@ -451,7 +451,9 @@ def run_zband(args):
                      "frac": tflops / float(peaks["bf16_tflops"]),
                      "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
                      "flops_per_launch": 2.0 * macs, "traffic": zband_traffic()},
-        "clocks": clk.summary(), "gpu_launches": args.steps * 5,
+        # per step: median (1 init + 4 x (histogram, pick)) and the fused inference (10), the work
+        # list (3), and the list check + correlation when the list is not empty (2)
+        "clocks": clk.summary(), "gpu_launches": args.steps * (13 + (2 if points[0]["units"] > 0 else 0)),
     }
     print(json.dumps(line), flush=True)
     net.close()
