@@ -321,7 +321,9 @@ def run_batch(args):
         "hbm_roofline": {"achieved": plane_bytes / (ms * 1e-3) / 1e9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                          "frac": plane_bytes / (ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
                          "peak_source": f"hbm_gbs ({peak_src})", "bytes_per_launch": plane_bytes},
-        "clocks": clk.summary(), "gpu_launches": args.steps,
+        # one persistent launch per step at 512 / 2048; one launch per spectrum at the other lengths
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps * (1 if best in (512, 2048) else int(args.batch_count)),
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
     print(json.dumps(line), flush=True)
