@@ -205,8 +205,8 @@ class Plan:
                "fdas_convolve_power")
 
     def convolve_power_tc(self, spectrum, plane, precision: str = "bf16", stream=None):
-        """Async: as convolve_power with the inverse transforms on the tensor cores (seg_len 2048;
-        precision "bf16" or "fp16", operands split into hi + lo)."""
+        """Async: as convolve_power with the segment transforms on the tensor cores (seg_len 2048;
+        precision "bf16" or "fp16", operands split into hi + lo; two launches)."""
         prec = _tc_precision(precision)
         _check(lib().fdas_convolve_power_tc(self._h, _ptr(spectrum), _ptr(plane), prec, _stream(stream)),
                "fdas_convolve_power_tc")

@@ -356,3 +356,38 @@ def test_maximum_spectrum_length_sampled(dev):
         del plane
     del d_spec
     torch.cuda.empty_cache()
+
+
+def test_two_plans_on_two_streams_match_sequential_runs(dev):
+    """Plans are independent: two plans with different geometries (L = 2048 and L = 1024), each
+    launched three times on its own stream while the other runs, give planes bit-identical to
+    their sequential runs (the kernels are deterministic)."""
+    import torch
+    from paper_1711_10855_gb300 import fdas
+    cases = [(200000, 40, 2, 2048, 512, 11), (150000, 30, 2, 1024, 256, 12)]
+    plans, specs, seq, conc = [], [], [], []
+    try:
+        for n, zmax, zstep, L, m, seed in cases:
+            plan = fdas.Plan(n, zmax, zstep, L, m)
+            plan.build_templates()
+            plans.append(plan)
+            specs.append(to_device(synth.noise_spectrum(n, seed=seed), dev))
+        for plan, spec, (n, *_rest) in zip(plans, specs, cases):
+            out = torch.empty((plan.n_z, n), dtype=torch.float32, device=dev)
+            plan.convolve_power(spec, out)
+            plan.check()
+            seq.append(out)
+        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        for plan, (n, *_rest) in zip(plans, cases):
+            conc.append(torch.full((plan.n_z, n), float("nan"), dtype=torch.float32, device=dev))
+        torch.cuda.synchronize(dev)
+        for _ in range(3):
+            for plan, spec, out, st in zip(plans, specs, conc, streams):
+                plan.convolve_power(spec, out, st)
+        for plan, st in zip(plans, streams):
+            plan.check(st)
+        for a, b in zip(seq, conc):
+            assert torch.equal(a, b)
+    finally:
+        for plan in plans:
+            plan.close()
