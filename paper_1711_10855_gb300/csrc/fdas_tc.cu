@@ -50,7 +50,8 @@ constexpr int kLbo64 = 8 * 128;     // K-chunk stride of a 64-row matrix
 constexpr int kLboA2 = 16 * 128 + 16;
 constexpr int kW1Bytes = 128 * 128 * 2, kW2Bytes = 64 * 64 * 2, kYBytes = 128 * 128 * 2, kA2Tile = 8 * kLboA2;
 constexpr int kOffW1h = 0, kOffW1l = kOffW1h + kW1Bytes, kOffW2h = kOffW1l + kW1Bytes, kOffW2l = kOffW2h + kW2Bytes;
-constexpr int kOffTw = kOffW2l + kW2Bytes;           // twist w2048^(k1 n2) at k1 * 64 + n2 (float2)
+// twist w2048^(k1 n2) for the k1 pair (2j, 2j+1) at float4 j * 64 + n2: (re, re, im, im)
+constexpr int kOffTw = kOffW2l + kW2Bytes;
 constexpr int kOffY = kOffTw + kTL * 8;              // Y hi | lo
 constexpr int kOffA2 = kOffY + 2 * kYBytes;          // A2 tiles: hi 0, hi 1, lo 0, lo 1
 constexpr int kOffMisc = kOffA2 + 4 * kA2Tile;       // mbarriers, TMEM slot, reduction scratch
@@ -67,16 +68,22 @@ struct TcType;
 template <>
 struct TcType<0> {
   using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
   static constexpr uint32_t fmt = 1;
   __device__ static T cvt(float x) { return __float2bfloat16_rn(x); }
   __device__ static float back(T x) { return __bfloat162float(x); }
+  __device__ static T2 cvt2(float2 x) { return __float22bfloat162_rn(x); }
+  __device__ static float2 back2(T2 x) { return __bfloat1622float2(x); }
 };
 template <>
 struct TcType<1> {
   using T = __half;
+  using T2 = __half2;
   static constexpr uint32_t fmt = 0;
   __device__ static T cvt(float x) { return __float2half_rn(x); }
   __device__ static float back(T x) { return __half2float(x); }
+  __device__ static T2 cvt2(float2 x) { return __float22half2_rn(x); }
+  __device__ static float2 back2(T2 x) { return __half22float2(x); }
 };
 
 // Eight consecutive K elements of one row (16 bytes of a core-matrix row), hi and lo parts.
@@ -84,13 +91,14 @@ template <int PREC>
 __device__ __forceinline__ void split_store8(unsigned char* hi, unsigned char* lo, int off, const float* x) {
   using TT = TcType<PREC>;
   union {
-    typename TT::T h[8];
+    typename TT::T2 h[4];
     uint4 u;
   } H, Lo;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    H.h[j] = TT::cvt(x[j]);
-    Lo.h[j] = TT::cvt(x[j] - TT::back(H.h[j]));
+  for (int j = 0; j < 4; ++j) {   // pairs: packed conversions and a packed subtraction
+    const float2 x2 = make_float2(x[2 * j], x[2 * j + 1]);
+    H.h[j] = TT::cvt2(x2);
+    Lo.h[j] = TT::cvt2(sub2(x2, TT::back2(H.h[j])));
   }
   *reinterpret_cast<uint4*>(hi + off) = H.u;
   *reinterpret_cast<uint4*>(lo + off) = Lo.u;
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_convolve_kernel(const TcPara
   using TT = TcType<PREC>;
   constexpr uint32_t kIdesc1 = tc_idesc(TT::fmt, 128, 128), kIdesc2 = tc_idesc(TT::fmt, 128, 2 * kTNV);
   extern __shared__ __align__(1024) unsigned char sm[];
-  const float2* sTw = reinterpret_cast<const float2*>(sm + kOffTw);
+  const float4* sTw = reinterpret_cast<const float4*>(sm + kOffTw);
   unsigned char* sY = sm + kOffY;
   unsigned char* sA2 = sm + kOffA2;
   uint64_t* bar1 = reinterpret_cast<uint64_t*>(sm + kOffMisc);        // stage-1 MMAs done
@@ -186,19 +194,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_convolve_kernel(const TcPara
   const int64_t U = p.units;
   const int64_t u0 = (int64_t)blockIdx.x * U / gridDim.x, u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
   if (u1 <= u0) return;
-  // DFT matrices, and the twist transposed to k1 * 64 + n2 (times 2^-6 for FP16; conjugated for
-  // the forward pass), once per CTA
+  // DFT matrices, and the twist in k1 pairs (times 2^-6 for FP16; conjugated for the forward
+  // pass), once per CTA
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.mats);
     uint4* dst = reinterpret_cast<uint4*>(sm + kOffW1h);
     for (int i = tid; i < kMatBytes / 16; i += kTcThreads) dst[i] = __ldg(src + i);
     // the plan's table holds w2048^(k1 n2) at float ((n2 % 32) * 32 + k1) * 4 + n2 / 32, Im + 2
     const float* tw = reinterpret_cast<const float*>(p.twist);
-    float2* tdst = reinterpret_cast<float2*>(sm + kOffTw);
-    const float s2 = PREC == 1 ? 0.015625f : 1.f;
-    for (int i = tid; i < kTL; i += kTcThreads) {
-      const int k1 = i >> 6, n2 = i & 63, off = ((n2 & 31) * 32 + k1) * 4 + (n2 >> 5);
-      tdst[i] = make_float2(__ldg(tw + off) * s2, __ldg(tw + off + 2) * (FWD ? -s2 : s2));
+    float4* tdst = reinterpret_cast<float4*>(sm + kOffTw);
+    const float s2 = PREC == 1 ? 0.015625f : 1.f, s2i = FWD ? -s2 : s2;
+    for (int i = tid; i < kTL / 2; i += kTcThreads) {
+      const int j = i >> 6, n2 = i & 63;
+      const int off0 = ((n2 & 31) * 32 + 2 * j) * 4 + (n2 >> 5), off1 = off0 + 4;   // k1 = 2j, 2j + 1
+      tdst[i] = make_float4(__ldg(tw + off0) * s2, __ldg(tw + off1) * s2, __ldg(tw + off0 + 2) * s2i,
+                            __ldg(tw + off1 + 2) * s2i);
     }
   }
   if (tid == 0) {
@@ -392,10 +402,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_convolve_kernel(const TcPara
       tmem_wait_ld();
       const float send = part ? -1.f : 1.f;
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) {
-        const float w = __shfl_xor_sync(0xffffffffu, v[k1] * send, 1);
-        const float2 tw = sTw[k1 * 64 + n2];
-        o[k1] = fmaf(w, tw.y, v[k1] * tw.x);
+      for (int j = 0; j < 16; ++j) {   // k1 = 2j, 2j + 1 as packed pairs
+        const float2 v2 = make_float2(v[2 * j], v[2 * j + 1]);
+        const float2 sv = mul2(v2, make_float2(send, send));
+        const float2 w2 = make_float2(__shfl_xor_sync(0xffffffffu, sv.x, 1), __shfl_xor_sync(0xffffffffu, sv.y, 1));
+        const float4 tw = sTw[j * 64 + n2];
+        const float2 o2 = fma2(w2, make_float2(tw.z, tw.w), mul2(v2, make_float2(tw.x, tw.y)));
+        o[2 * j] = o2.x;
+        o[2 * j + 1] = o2.y;
       }
     } else {
 #pragma unroll
@@ -437,11 +451,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_convolve_kernel(const TcPara
       float* row = p.plane + (size_t)(z0 + zl) * p.n_bins + s * (int64_t)p.V;
       const int64_t lim64 = p.n_bins - s * (int64_t)p.V < (int64_t)p.V ? p.n_bins - s * (int64_t)p.V : (int64_t)p.V;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < 16; j += 2) {   // n1 pairs: packed |y|^2
+        const float2 r2 = make_float2(re[j], re[j + 1]), i2 = make_float2(im[j], im[j + 1]);
+        float2 pw = fma2(r2, r2, mul2(i2, i2));
+        if constexpr (PREC == 1) pw = mul2(pw, make_float2(post, post));
         const int n = n2 + kTN2 * (16 * g + j);
-        float pw = fmaf(re[j], re[j], im[j] * im[j]);
-        if constexpr (PREC == 1) pw *= post;
-        if (n < lim64) __stcs(row + n, pw);
+        if (n < lim64) __stcs(row + n, pw.x);
+        if (n + kTN2 < lim64) __stcs(row + n + kTN2, pw.y);
       }
     }
   };
