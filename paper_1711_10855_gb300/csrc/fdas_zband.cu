@@ -790,6 +790,13 @@ struct fdas_zband {
   float* scale = nullptr;    // ln 2 / median |A|^2
   int* status = nullptr;     // bit 0: a bounded wait of the inference kernel gave up
   int step = 0;
+  // fdas_zband_propose as a CUDA graph of its launches, captured for these arguments
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* cap_spec = nullptr;
+  int64_t cap_n = 0;
+  const void* cap_logits = nullptr;
 };
 
 namespace {
@@ -797,6 +804,9 @@ void free_zband(fdas_zband* z) {
   void* ptrs[] = {z->p,  z->ph,     z->g,   z->m,      z->v,    z->a1,   z->a2,      z->a3,    z->d1,
                   z->d2, z->pooled, z->arg, z->logits, z->dlog, z->loss, z->sel, z->scale, z->status};
   for (void* q : ptrs) cudaFree(q);
+  if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
+  if (z->graph) cudaGraphDestroy(z->graph);
+  if (z->capture_stream) cudaStreamDestroy(z->capture_stream);
   delete z;
 }
 
@@ -1008,14 +1018,10 @@ int fdas_zband_predict(fdas_zband* z, const float* d_windows, int batch, int hal
   return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
-int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, float* d_logits,
-                       fdas_stream_t stream) {
-  if (!z || !d_spectrum || !d_logits || n_bins < 1 || n_bins > (int64_t(1) << 30)) return FDAS_ERR_INVALID;
+// The launches of one proposal (median passes, then the fused inference) on `st`.
+static cudaError_t launch_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, float* d_logits,
+                                  cudaStream_t st) {
   const int hop = z->Wd / 2;
-  if (hop % 128 != 0 || hop > kMaxHop) return FDAS_ERR_INVALID;
-  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u))
-    return FDAS_ERR_ALIGN;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t nb = (n_bins + hop - 1) / hop;
   launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->sel, z->scale, st);
   ProposeParams q;
@@ -1043,7 +1049,50 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
     case 384: propose_kernel<384><<<grid, 256, kProposeSmem, st>>>(q); break;
     default: propose_kernel<512><<<grid, 256, kProposeSmem, st>>>(q); break;
   }
-  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return cudaGetLastError();
+}
+
+int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, float* d_logits,
+                       fdas_stream_t stream) {
+  if (!z || !d_spectrum || !d_logits || n_bins < 1 || n_bins > (int64_t(1) << 30)) return FDAS_ERR_INVALID;
+  const int hop = z->Wd / 2;
+  if (hop % 128 != 0 || hop > kMaxHop) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u))
+    return FDAS_ERR_ALIGN;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // ten launches replayed as one graph: captured again when the spectrum, its length or the
+  // logits buffer change (the weights are read through fixed pointers, so training needs none)
+  if (!(z->graph_exec && z->cap_spec == d_spectrum && z->cap_n == n_bins && z->cap_logits == d_logits)) {
+    if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
+    if (z->graph) cudaGraphDestroy(z->graph);
+    z->graph_exec = nullptr;
+    z->graph = nullptr;
+    if (!z->capture_stream && cudaStreamCreateWithFlags(&z->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      z->capture_stream = nullptr;
+      return FDAS_ERR_CUDA;
+    }
+    if (cudaStreamBeginCapture(z->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+    const cudaError_t le = launch_propose(z, d_spectrum, n_bins, d_logits, z->capture_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(z->capture_stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return FDAS_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&z->graph_exec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      z->graph_exec = nullptr;
+      cudaGetLastError();
+      return FDAS_ERR_CUDA;
+    }
+    z->graph = g;
+    z->cap_spec = d_spectrum;
+    z->cap_n = n_bins;
+    z->cap_logits = d_logits;
+  }
+  return cudaGraphLaunch(z->graph_exec, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 int fdas_zband_check(fdas_zband* z, fdas_stream_t stream) {

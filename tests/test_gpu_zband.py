@@ -276,3 +276,27 @@ def test_convolve_power_units_rejects_bad_lists_on_the_device():
         assert not torch.isnan(part[0, :10]).any()
         with pytest.raises(fdas.FdasError):
             plan.convolve_power_units(spec, part, good, 0)
+
+
+def test_propose_graph_replay_follows_new_weights_and_buffers():
+    """The proposal replays a captured graph: new weights on the same buffers, and a new logits
+    buffer (a new capture), give exactly what a fresh net with those weights gives."""
+    Z, W, n = 21, 1024, 30000
+    spec = dev(chirp_spectrum(n, 71).view(np.float32).copy())
+    v1, _ = make_params(Z, 72)
+    v2, _ = make_params(Z, 73)
+    with fdas.ZBand(W, Z, 4) as net, fdas.ZBand(W, Z, 4) as fresh:
+        nb = net.n_blocks(n)
+        a = torch.empty((nb, Z), dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        ref = torch.empty_like(a)
+        net.set_params(v1)
+        net.propose(spec, n, a)
+        net.set_params(v2)
+        net.propose(spec, n, a)          # replay with new weights
+        net.propose(spec, n, b)          # another logits buffer: captured again
+        net.check()
+        fresh.set_params(v2)
+        fresh.propose(spec, n, ref)
+        fresh.check()
+        assert torch.equal(a, ref) and torch.equal(b, ref)
