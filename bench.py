@@ -390,8 +390,37 @@ def run_zband(args):
         n_units = ps.search(spec, part, thr)
         plan.check()
         rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
-        points.append({"threshold": thr, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
-                       "units": int(n_units)})
+        point = {"threshold": thr, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
+                 "segment_fraction": ps.segment_fraction, "units": int(n_units)}
+        wall = []   # the whole synchronised path at this threshold (L2 flushed before each run)
+        for _ in range(10):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            ps.search(spec, part, thr)
+            torch.cuda.synchronize(dev)
+            wall.append((time.perf_counter() - t1) * 1e3)
+        point["ms"] = statistics.median(wall)
+        points.append(point)
+    # the same thresholds without segment masks (every segment of a listed unit's group computed)
+    ps_group = zb.ProposalSearch(net, plan, segment_masks=False)
+    group_points = []
+    for thr in args.zband_thresholds:
+        part.fill_(float("nan"))
+        n_units = ps_group.search(spec, part, thr)
+        plan.check()
+        rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
+        wall = []
+        for _ in range(10):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            ps_group.search(spec, part, thr)
+            torch.cuda.synchronize(dev)
+            wall.append((time.perf_counter() - t1) * 1e3)
+        group_points.append({"threshold": thr, "recall": rec, "unit_fraction": ps_group.unit_fraction,
+                             "units": int(n_units), "ms": statistics.median(wall)})
+    del ps_group
     # a denser check of recall: 2^22 bins with a chirp in every 16th block (SNR as in training)
     rng = np.random.default_rng(171110859)
     gen = torch.Generator(device=dev)
@@ -407,7 +436,7 @@ def run_zband(args):
         plan.check()
         rec, n_det, _, _ = zb.recall(torch, full, part, spec2, w.n_bins)
         dense_points.append({"threshold": t, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
-                             "units": int(n_units)})
+                             "segment_fraction": ps.segment_fraction, "units": int(n_units)})
     del spec2
     thr = args.zband_thresholds[0]
     for _ in range(args.warmup):
@@ -444,7 +473,7 @@ def run_zband(args):
                    "timing": "host wall clock around the synchronised path (it reads the list length)"},
         "recall": points[0]["recall"], "unit_fraction": points[0]["unit_fraction"],
         "full_search_ms": full_ms, "full_search_cells_per_s": cells / (full_ms * 1e-3),
-        "propose_ms": propose_ms, "operating_points": points,
+        "propose_ms": propose_ms, "operating_points": points, "operating_points_without_segment_masks": group_points,
         "dense_operating_points": {"spectrum": f"2^22 bins, {int(chirps["z"].shape[1])} chirps (one per 16 blocks), "
                                                f"SNR {args.zband_snr[0]:g}-{args.zband_snr[1]:g} {args.zband_snr_dist}",
                                    "points": dense_points},

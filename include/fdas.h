@@ -252,6 +252,14 @@ int fdas_batch_autotune(int count, const int64_t* n_bins, const int* zmax, int z
 int fdas_plan_group_segments(const fdas_plan* plan);
 int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d_plane, const int32_t* d_units,
                               int64_t n_units, fdas_stream_t stream);
+/* As fdas_convolve_power_units with a segment mask per list entry (device uint16 array parallel
+ * to d_units, 2-byte aligned, or NULL for all segments): bit j set = segment g*G + j of the
+ * entry's group is computed for its template; only the cells of those segments (bins
+ * [(g*G+j)*V, (g*G+j+1)*V)) are written.  A warp whose segments are all unset skips its
+ * transforms, so sparse masks cost less. */
+int fdas_convolve_power_units_masked(fdas_plan* plan, const float* d_spectrum, float* d_plane,
+                                     const int32_t* d_units, const uint16_t* d_masks, int64_t n_units,
+                                     fdas_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Learned z-band proposal (no counterpart in the paper): a 1-D convolutional network over the
@@ -333,6 +341,15 @@ int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z);
 int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
                           int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,
                           int64_t* host_count, fdas_stream_t stream);
+/* As fdas_zband_work_units, per segment: group g holds G (1..16) segments of seg_bins = V bins;
+ * segment j is proposed for template z when a block meets [(g*G+j)*V - h, (g*G+j+1)*V + h) with
+ * sigmoid(logit) >= threshold, and unit g*Z + z is listed when any of its G segments is.
+ * d_masks (device uint16, room for n_groups*Z, 2-byte aligned; may be NULL) receives each listed
+ * unit's segment bits, for fdas_convolve_power_units_masked.  fdas_zband_work_units is the case
+ * G = 1, seg_bins = group_bins. */
+int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
+                                 int64_t seg_bins, int G, int h, int64_t n_groups, int32_t* d_units,
+                                 uint16_t* d_masks, void* d_scratch, int64_t* host_count, fdas_stream_t stream);
 int fdas_zband_destroy(fdas_zband* net);
 
 /*

@@ -180,3 +180,26 @@ def work_units(logits: np.ndarray, threshold: float, hop: int, group_bins: int, 
             if any(keep[w, z] for w in range(nw) if w * hop < hi and (w + 1) * hop > lo):
                 units.append(g * Z + z)
     return np.asarray(units, dtype=np.int64)
+
+
+def work_unit_masks(logits: np.ndarray, threshold: float, hop: int, seg_bins: int, segments: int, h: int,
+                    n_groups: int):
+    """(units, masks): segment j of group g (outputs [(g*G+j)*V, (g*G+j+1)*V), V = seg_bins,
+    G = segments) is proposed for template z when a block w whose bins [w*hop, (w+1)*hop) meet
+    [(g*G+j)*V - h, (g*G+j+1)*V + h) has sigmoid(logit[w, z]) >= threshold; unit g*Z + z is listed
+    (ascending) when any of its segments is, with mask bit j set for each proposed segment."""
+    nw, Z = logits.shape
+    keep = 1.0 / (1.0 + np.exp(-np.asarray(logits, dtype=np.float64))) >= threshold
+    units, masks = [], []
+    for g in range(n_groups):
+        for z in range(Z):
+            m = 0
+            for j in range(segments):
+                s = g * segments + j
+                lo, hi = s * seg_bins - h, (s + 1) * seg_bins + h
+                if any(keep[w, z] for w in range(nw) if w * hop < hi and (w + 1) * hop > lo):
+                    m |= 1 << j
+            if m:
+                units.append(g * Z + z)
+                masks.append(m)
+    return np.asarray(units, dtype=np.int64), np.asarray(masks, dtype=np.int64)

@@ -399,13 +399,14 @@ int fdas_plan_group_segments(const fdas_plan* p) {
   return G > 0 ? G : FDAS_ERR_INVALID;
 }
 
-int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_units,
-                              int64_t n_units, fdas_stream_t stream) {
+int fdas_convolve_power_units_masked(fdas_plan* p, const float* d_spectrum, float* d_plane,
+                                     const int32_t* d_units, const uint16_t* d_masks, int64_t n_units,
+                                     fdas_stream_t stream) {
   if (!p || !d_spectrum || !d_plane || !d_units || n_units < 1) return FDAS_ERR_INVALID;
   if (!p->built) return FDAS_ERR_NOT_BUILT;
   if (fdas::batch_segments_per_cta(p->L) == 0) return FDAS_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u) ||
-      (reinterpret_cast<uintptr_t>(d_units) & 3u))
+      (reinterpret_cast<uintptr_t>(d_units) & 3u) || (reinterpret_cast<uintptr_t>(d_masks) & 1u))
     return FDAS_ERR_ALIGN;
   fdas::ConvParams q;
   q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
@@ -419,8 +420,14 @@ int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_pl
   q.Z = p->Z;
   q.V = p->V;
   q.h = p->h;
-  cudaError_t e = fdas::launch_units(p->L, q, d_units, n_units, p->sm_count, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = fdas::launch_units(p->L, q, d_units, d_masks, n_units, p->sm_count,
+                                     reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_units,
+                              int64_t n_units, fdas_stream_t stream) {
+  return fdas_convolve_power_units_masked(p, d_spectrum, d_plane, d_units, nullptr, n_units, stream);
 }
 
 int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fdas_stream_t stream) {

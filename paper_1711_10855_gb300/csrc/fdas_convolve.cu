@@ -532,6 +532,22 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     });
     tmem_wait_st();
   }
+  // release template slot `slot` of position i; the last of the W consumers refills it R positions
+  // ahead
+  auto release_slot = [&](int64_t i, int slot) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const unsigned old = atomicAdd(&cnt[slot], 1u);
+      if ((old + 1u) % (unsigned)W == 0u) {
+        __threadfence_block();
+        if (i + R < npos) {
+          fence_proxy_async_smem();
+          issue_template(i + R);
+        }
+      }
+    }
+  };
   tmem_fence_before_sync();
   int alive = 1;
   uint32_t seg_phase = 0;
@@ -626,6 +642,22 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
       if constexpr (LIST) z = unit_at(u0 + i) % d.Z;
       else z = z_first + (int64_t)(i - a);
       const float4* st4 = reinterpret_cast<const float4*>(sT + (size_t)slot * L);
+      // a masked list entry: a warp none of whose segments is listed skips the transform (it still
+      // releases the slot); lanes of an unlisted segment store nothing
+      bool warp_on = true, group_on = true;
+      if constexpr (LIST) {
+        if (p.unit_mask) {
+          const unsigned wm = ((unsigned)__ldg(p.unit_mask + u0 + i) >> (warp * Cfg::F)) & ((1u << Cfg::F) - 1u);
+          warp_on = wm != 0u;
+          group_on = ((wm >> gw) & 1u) != 0u;
+        }
+      }
+
+      if (!warp_on) {   // the slot is released unread
+        release_slot(i, slot);
+        continue;
+      }
+      const int lim_z = group_on ? lim : 0;
 
       // a4: Y = X (TMEM) * T (shared ring), packed pairs in bit-reversed order
       cp2 v[H2];
@@ -648,19 +680,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
           v[bitrev(2 * pp, Cfg::LOG_N2)] = cmul2(x, cp2_from(t[q]));
         });
       });
-      // release the template slot; the last of the W consumers refills it R positions ahead
-      __syncwarp();
-      if (lane == 0) {
-        __threadfence_block();
-        const unsigned old = atomicAdd(&cnt[slot], 1u);
-        if ((old + 1u) % (unsigned)W == 0u) {
-          __threadfence_block();
-          if (i + R < npos) {
-            fence_proxy_async_smem();
-            issue_template(i + R);
-          }
-        }
-      }
+      release_slot(i, slot);
       // a5: inverse FFT
       fft_split_pairs<Cfg::N2, +1>(v);
       apply_twist_tmem<Cfg, false>(v, tw_addr);
@@ -672,8 +692,8 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
           const float2 pw = power2(y);
           const int n_lo = k1 + Cfg::N2 * n1;
           const int n_hi = n_lo + N1;
-          if (n_lo < lim) __stcs(row + n_lo, pw.x);
-          if (n_hi < lim) __stcs(row + n_hi, pw.y);
+          if (n_lo < lim_z) __stcs(row + n_lo, pw.x);
+          if (n_hi < lim_z) __stcs(row + n_hi, pw.y);
         }
       });
     }
@@ -847,8 +867,8 @@ __global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limi
   }
 }
 
-cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, int64_t n_units, int sm_count,
-                         cudaStream_t st) {
+cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const uint16_t* masks, int64_t n_units,
+                         int sm_count, cudaStream_t st) {
   const int G = batch_segments_per_cta(L);
   if (G == 0 || n_units < 1) return cudaErrorInvalidValue;
   const int64_t ngroups = (p.nseg + G - 1) / G;
@@ -873,6 +893,7 @@ cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, int64
   q.single.z_off = 0;
   q.units = n_units;
   q.unit_list = units;
+  q.unit_mask = masks;
   q.V = p.V;
   q.h = p.h;
   return launch_batch(L, q, sm_count, st);

@@ -44,6 +44,8 @@ struct BatchParams {
   int64_t units;            // total units over all spectra (or entries of unit_list)
   const int32_t* unit_list; // single spectrum only: ascending units g*Z + z to compute, or nullptr: all
   int V, h;
+  // with unit_list: per entry, bit j = segment j of the unit's group is computed (nullptr: all)
+  const uint16_t* unit_mask = nullptr;
 };
 
 // Parameters of the forward-transform-only kernel (steps a2 + a3, for tests).
@@ -69,7 +71,7 @@ int batch_segments_per_cta(int L);
 // Descriptor-driven launch (L with batch_segments_per_cta(L) > 0).
 cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t stream);
 // Single spectrum restricted to a work list of units g*Z + z (ascending).
-cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, int64_t n_units, int sm_count,
+cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const uint16_t* masks, int64_t n_units, int sm_count,
                          cudaStream_t stream);
 
 // Launch helpers (defined in fdas_convolve.cu).  Return a cudaError_t from the launch.

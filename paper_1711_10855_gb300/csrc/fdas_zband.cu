@@ -358,13 +358,15 @@ __global__ void to_half_kernel(const float* p, __half* h, int n) {
   if (i < n) h[i] = __float2half_rn(p[i]);
 }
 
-// Proposal -> correlation work list.  Segment group g (G segments of V bins) is proposed for
-// template z if any window whose central bins [w*hop, (w+1)*hop) meet the bins the group's
-// outputs can draw on, [g*G*V - h, (g+1)*G*V + h), has sigmoid(logit_z) >= threshold.
-__global__ void group_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, int hop, int64_t group_bins,
-                                   int h, int n_groups, unsigned char* flags, int* counts) {
+// Proposal -> correlation work list.  Segment j of group g (G segments of V bins: outputs
+// [(gG+j)V, (gG+j+1)V)) is proposed for template z if any window whose central bins
+// [w*hop, (w+1)*hop) meet the bins its outputs can draw on, [(gG+j)V - h, (gG+j+1)V + h), has
+// sigmoid(logit_z) >= threshold; mask[g][z] holds those G bits and unit (g, z) is listed when
+// any is set.
+__global__ void group_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, int hop, int64_t seg_bins,
+                                   int G, int h, int n_groups, uint16_t* masks, int* counts) {
   const int g = blockIdx.x;
-  const int64_t lo = (int64_t)g * group_bins - h, hi = (int64_t)(g + 1) * group_bins + h;
+  const int64_t lo = (int64_t)g * G * seg_bins - h, hi = ((int64_t)g + 1) * G * seg_bins + h;
   int w0 = (int)((lo > 0 ? lo : 0) / hop);
   int w1 = (int)((hi + hop - 1) / hop);
   if (w1 > n_win) w1 = n_win;
@@ -372,10 +374,17 @@ __global__ void group_flags_kernel(const float* logits, int n_win, int Z, float 
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   for (int z = threadIdx.x; z < Z; z += blockDim.x) {
-    unsigned char f = 0;
-    for (int w = w0; w < w1 && !f; ++w) f = logits[(size_t)w * Z + z] >= logit_thr;
-    flags[(size_t)g * Z + z] = f;
-    if (f) atomicAdd(&cnt, 1);
+    unsigned m = 0u;
+    for (int w = w0; w < w1; ++w) {
+      if (!(logits[(size_t)w * Z + z] >= logit_thr)) continue;
+      const int64_t b0 = (int64_t)w * hop, b1 = b0 + hop;   // the window's central bins
+      for (int j = 0; j < G; ++j) {
+        const int64_t s0 = ((int64_t)g * G + j) * seg_bins - h, s1 = ((int64_t)g * G + j + 1) * seg_bins + h;
+        if (b0 < s1 && b1 > s0) m |= 1u << j;
+      }
+    }
+    masks[(size_t)g * Z + z] = (uint16_t)m;
+    if (m) atomicAdd(&cnt, 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) counts[g] = cnt;
@@ -419,16 +428,18 @@ __global__ void __launch_bounds__(1024) scan_counts_kernel(const int* counts, in
   if (tid == 1023) *total = run;
 }
 
-// units[offset_g + k] = g*Z + z for the k-th proposed z of group g (increasing z): one block of
-// 256 threads per group, each flag placed by the popcount of the flags before it.
-__global__ void __launch_bounds__(256) write_units_kernel(const unsigned char* flags, const int64_t* offsets, int Z,
-                                                          int32_t* units) {
+// units[offset_g + k] = g*Z + z for the k-th proposed z of group g (increasing z), and its
+// segment mask when out_masks is set: one block of 256 threads per group, each unit placed by
+// the popcount of the proposed templates before it.
+__global__ void __launch_bounds__(256) write_units_kernel(const uint16_t* masks, const int64_t* offsets, int Z,
+                                                          int32_t* units, uint16_t* out_masks) {
   __shared__ int warp_cnt[8];
   const int g = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t base = offsets[g];
   for (int z0 = 0; z0 < Z; z0 += 256) {
     const int z = z0 + (int)threadIdx.x;
-    const bool f = z < Z && flags[(size_t)g * Z + z] != 0;
+    const unsigned mz = z < Z ? masks[(size_t)g * Z + z] : 0u;
+    const bool f = mz != 0u;
     const unsigned m = __ballot_sync(0xffffffffu, f);
     if (lane == 0) warp_cnt[wid] = __popc(m);
     __syncthreads();
@@ -438,7 +449,11 @@ __global__ void __launch_bounds__(256) write_units_kernel(const unsigned char* f
       before += i < wid ? warp_cnt[i] : 0;
       all += warp_cnt[i];
     }
-    if (f) units[base + before + __popc(m & ((1u << lane) - 1u))] = (int32_t)((int64_t)g * Z + z);
+    if (f) {
+      const int64_t at = base + before + __popc(m & ((1u << lane) - 1u));
+      units[at] = (int32_t)((int64_t)g * Z + z);
+      if (out_masks) out_masks[at] = (uint16_t)mz;
+    }
     base += all;
     __syncthreads();
   }
@@ -1130,11 +1145,11 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
   return rc;
 }
 
-// Work-list scratch: offsets (int64, n_groups + 1), counts (int32, n_groups), flags (n_groups * Z
-// bytes), each 16-byte aligned.
+// Work-list scratch: offsets (int64, n_groups + 1), counts (int32, n_groups), segment masks
+// (uint16, n_groups * Z), each 16-byte aligned.
 static int64_t align16(int64_t x) { return (x + 15) & ~(int64_t)15; }
 static int64_t units_scratch_bytes(int64_t n_groups, int Z) {
-  return align16(8 * (n_groups + 1)) + align16(4 * n_groups) + align16(n_groups * (int64_t)Z);
+  return align16(8 * (n_groups + 1)) + align16(4 * n_groups) + align16(2 * n_groups * (int64_t)Z);
 }
 
 int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z) {
@@ -1142,14 +1157,16 @@ int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z) {
   return units_scratch_bytes(n_groups, Z);
 }
 
-int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
-                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,
-                          int64_t* host_count, fdas_stream_t stream) {
+int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
+                                 int64_t seg_bins, int G, int h, int64_t n_groups, int32_t* d_units,
+                                 uint16_t* d_masks, void* d_scratch, int64_t* host_count, fdas_stream_t stream) {
   if (!d_logits || !d_units || !host_count || n_windows < 1 || n_windows > (1 << 30) || Z < 1 ||
-      !(threshold > 0.f && threshold < 1.f) || hop < 1 || group_bins < 1 || h < 0 || n_groups < 1 ||
-      n_groups > (1 << 24) || (int64_t)n_groups * Z > INT32_MAX)
+      !(threshold > 0.f && threshold < 1.f) || hop < 1 || seg_bins < 1 || G < 1 || G > 16 || h < 0 ||
+      n_groups < 1 || n_groups > (1 << 24) || (int64_t)n_groups * Z > INT32_MAX ||
+      seg_bins * G > (int64_t(1) << 40))
     return FDAS_ERR_INVALID;
-  if (reinterpret_cast<uintptr_t>(d_scratch) & 15u) return FDAS_ERR_ALIGN;
+  if ((reinterpret_cast<uintptr_t>(d_scratch) & 15u) || (reinterpret_cast<uintptr_t>(d_masks) & 1u))
+    return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float logit_thr = logf(threshold / (1.f - threshold));
   const int64_t bytes = units_scratch_bytes(n_groups, Z);
@@ -1161,11 +1178,11 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
   }
   int64_t* offsets = reinterpret_cast<int64_t*>(scratch);
   int* counts = reinterpret_cast<int*>(scratch + align16(8 * (n_groups + 1)));
-  unsigned char* flags = scratch + align16(8 * (n_groups + 1)) + align16(4 * n_groups);
-  group_flags_kernel<<<(unsigned)n_groups, 256, 0, st>>>(d_logits, (int)n_windows, Z, logit_thr, hop, group_bins, h,
-                                                        (int)n_groups, flags, counts);
+  uint16_t* masks = reinterpret_cast<uint16_t*>(scratch + align16(8 * (n_groups + 1)) + align16(4 * n_groups));
+  group_flags_kernel<<<(unsigned)n_groups, 256, 0, st>>>(d_logits, (int)n_windows, Z, logit_thr, hop, seg_bins, G,
+                                                        h, (int)n_groups, masks, counts);
   scan_counts_kernel<<<1, 1024, 0, st>>>(counts, (int)n_groups, offsets, offsets + n_groups);
-  write_units_kernel<<<(unsigned)n_groups, 256, 0, st>>>(flags, offsets, Z, d_units);
+  write_units_kernel<<<(unsigned)n_groups, 256, 0, st>>>(masks, offsets, Z, d_units, d_masks);
   int rc = FDAS_OK;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(host_count, offsets + n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1173,6 +1190,14 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
     rc = FDAS_ERR_CUDA;
   if (own) cudaFreeAsync(scratch, st);
   return rc;
+}
+
+int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
+                          int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,
+                          int64_t* host_count, fdas_stream_t stream) {
+  // one segment of group_bins per group: the group's flag
+  return fdas_zband_work_units_masked(d_logits, n_windows, Z, threshold, hop, group_bins, 1, h, n_groups, d_units,
+                                      nullptr, d_scratch, host_count, stream);
 }
 
 int fdas_zband_destroy(fdas_zband* z) {

@@ -34,7 +34,8 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_zband_get_adam", "fdas_zband_set_adam", "fdas_zband_train_step", "fdas_zband_gradients",
             "fdas_zband_predict", "fdas_zband_propose", "fdas_zband_check", "fdas_zband_spectrum_windows",
             "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc",
-            "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes"]
+            "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes",
+            "fdas_convolve_power_units_masked", "fdas_zband_work_units_masked"]
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +98,11 @@ def lib() -> ctypes.CDLL:
             L.fdas_plan_group_segments.restype = i32
             L.fdas_convolve_power_units.argtypes = [vp, vp, vp, vp, i64, vp]
             L.fdas_convolve_power_units.restype = i32
+            L.fdas_convolve_power_units_masked.argtypes = [vp, vp, vp, vp, vp, i64, vp]
+            L.fdas_convolve_power_units_masked.restype = i32
+            L.fdas_zband_work_units_masked.argtypes = [vp, i64, i32, ctypes.c_float, i32, i64, i32, i32, i64, vp, vp,
+                                                       vp, vp, vp]
+            L.fdas_zband_work_units_masked.restype = i32
             f32 = ctypes.c_float
             L.fdas_zband_create.argtypes = [i32, i32, i32]
             L.fdas_zband_create.restype = vp
@@ -235,10 +241,16 @@ class Plan:
             raise FdasError(g, "fdas_plan_group_segments")
         return g
 
-    def convolve_power_units(self, spectrum, plane, units, n_units: int, stream=None):
-        """Only the listed work units g*Z + z (ascending int32 device tensor) are computed."""
-        _check(lib().fdas_convolve_power_units(self._h, _ptr(spectrum), _ptr(plane), _ptr(units), int(n_units),
-                                               _stream(stream)), "fdas_convolve_power_units")
+    def convolve_power_units(self, spectrum, plane, units, n_units: int, stream=None, masks=None):
+        """Only the listed work units g*Z + z (ascending int32 device tensor) are computed; with
+        `masks` (16-bit device tensor parallel to units) only the segments whose bits are set."""
+        if masks is None:
+            _check(lib().fdas_convolve_power_units(self._h, _ptr(spectrum), _ptr(plane), _ptr(units), int(n_units),
+                                                   _stream(stream)), "fdas_convolve_power_units")
+        else:
+            _check(lib().fdas_convolve_power_units_masked(self._h, _ptr(spectrum), _ptr(plane), _ptr(units),
+                                                          _ptr(masks), int(n_units), _stream(stream)),
+                   "fdas_convolve_power_units_masked")
 
     def template_taps(self, z_idx: int) -> np.ndarray:
         out = np.empty(2 * (self.tmpl_len + 1), dtype=np.float64)
@@ -377,10 +389,21 @@ def zband_work_units_scratch_bytes(n_groups: int, n_z: int) -> int:
 
 
 def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: int, group_bins: int, h: int,
-                     n_groups: int, units, stream=None, scratch=None) -> int:
+                     n_groups: int, units, stream=None, scratch=None, masks=None, segments: int = 1) -> int:
     """Async work list into `units`; returns its length (synchronises the stream).  `scratch`: a
     device buffer of zband_work_units_scratch_bytes bytes reused across calls (None: allocated
-    inside the call)."""
+    inside the call).  With `masks` (16-bit device tensor, room for n_groups * n_z), each listed
+    unit's bits for its `segments` segments of group_bins / segments bins."""
+    if masks is not None or segments != 1:
+        if group_bins % segments:
+            raise ValueError("group_bins must be a multiple of segments")
+        count = ctypes.c_int64(0)
+        _check(lib().fdas_zband_work_units_masked(_ptr(logits), int(n_windows), int(n_z), float(threshold),
+                                                  int(hop), int(group_bins // segments), int(segments), int(h),
+                                                  int(n_groups), _ptr(units), None if masks is None else _ptr(masks),
+                                                  None if scratch is None else _ptr(scratch), ctypes.byref(count),
+                                                  _stream(stream)), "fdas_zband_work_units_masked")
+        return count.value
     count = ctypes.c_int64(0)
     _check(lib().fdas_zband_work_units(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(hop),
                                        int(group_bins), int(h), int(n_groups), _ptr(units),

@@ -190,7 +190,7 @@ class ProposalSearch:
     """The proposal path for one plan: logits -> work list -> partial plane (async except the
     work-list length, which the host needs to size the launch)."""
 
-    def __init__(self, net: "fdas.ZBand", plan: "fdas.Plan", device=None):
+    def __init__(self, net: "fdas.ZBand", plan: "fdas.Plan", device=None, segment_masks: bool = True):
         import torch
         dev = device or torch.device("cuda")
         if net.window != WINDOW or net.n_out != plan.n_z:
@@ -203,25 +203,37 @@ class ProposalSearch:
         self.units = torch.empty(self.n_groups * plan.n_z, dtype=torch.int32, device=dev)
         self.scratch = torch.empty(fdas.zband_work_units_scratch_bytes(self.n_groups, plan.n_z), dtype=torch.uint8,
                                    device=dev)
+        # segment bits of each listed unit (None: every segment of a listed unit's group is computed)
+        self.masks = torch.empty(self.n_groups * plan.n_z, dtype=torch.int16, device=dev) if segment_masks else None
         self.n_units = 0
 
     def propose(self, spectrum, threshold: float) -> int:
         self.net.propose(spectrum, self.plan.n_bins, self.logits)
         self.n_units = fdas.zband_work_units(self.logits, self.n_blocks, self.plan.n_z, threshold, HOP,
                                              self.G * self.plan.valid, self.plan.tmpl_len // 2, self.n_groups,
-                                             self.units, scratch=self.scratch)
+                                             self.units, scratch=self.scratch, masks=self.masks,
+                                             segments=self.G if self.masks is not None else 1)
         return self.n_units
 
     def search(self, spectrum, plane, threshold: float) -> int:
         """Proposal plus the partial correlation into `plane` (cells outside the list untouched)."""
         n = self.propose(spectrum, threshold)
         if n > 0:
-            self.plan.convolve_power_units(spectrum, plane, self.units, n)
+            self.plan.convolve_power_units(spectrum, plane, self.units, n, masks=self.masks)
         return n
 
     @property
     def unit_fraction(self) -> float:
         return self.n_units / float(self.n_groups * self.plan.n_z)
+
+    @property
+    def segment_fraction(self) -> float:
+        """Fraction of (segment, template) pairs the last list computes (its set mask bits)."""
+        if self.masks is None:
+            return self.unit_fraction
+        m = self.masks[:self.n_units].cpu().numpy().astype(np.uint16)
+        bits = int(np.unpackbits(m.view(np.uint8)).sum())
+        return bits / float(self.plan.n_seg * self.plan.n_z)
 
 
 def recall(torch, full_plane, part_plane, spectrum, n_bins: int, det_power: float = DET_POWER):

@@ -137,7 +137,11 @@ def test_null_and_invalid_zband_calls(lib):
     lib.fdas_zband_work_units_scratch_bytes.restype = ctypes.c_int64
     lib.fdas_zband_work_units_scratch_bytes.argtypes = [ctypes.c_int64, ctypes.c_int]
     assert lib.fdas_zband_work_units_scratch_bytes(0, 201) == -1
-    assert lib.fdas_zband_work_units_scratch_bytes(342, 201) == 2752 + 1376 + 68752
+    # offsets int64 [343], counts int32 [342], segment masks uint16 [342 x 201], 16-byte aligned
+    assert lib.fdas_zband_work_units_scratch_bytes(342, 201) == 2752 + 1376 + 137488
+    assert lib.fdas_zband_work_units_masked(None, 4, 201, ctypes.c_float(0.5), 512, 1536, 8, 256, 2, None, None,
+                                            None, None, None) == -1
+    assert lib.fdas_convolve_power_units_masked(None, None, None, None, None, 1, None) == -1
     assert lib.fdas_zband_destroy(None) == 0
     assert lib.fdas_plan_group_segments(None) == -1
     assert lib.fdas_convolve_power_units(None, None, None, None, 1, None) == -1

@@ -300,3 +300,57 @@ def test_propose_graph_replay_follows_new_weights_and_buffers():
         fresh.propose(spec, n, ref)
         fresh.check()
         assert torch.equal(a, ref) and torch.equal(b, ref)
+
+
+@pytest.mark.parametrize("L,m,n_bins", [(2048, 512, 200_000), (512, 64, 70_004)])
+def test_masked_units_write_only_their_segments(L, m, n_bins):
+    """Segment masks: a listed unit computes only the segments whose bits are set (cells equal to
+    the full plane's, bit for bit) and leaves every other cell untouched; masks with a warp's
+    segments all unset (it skips its transforms), single bits, and all bits."""
+    zmax, zstep = 20, 2
+    spec = dev(synth.noise_spectrum(n_bins, 81))
+    with fdas.Plan(n_bins, zmax, zstep, L, m) as plan:
+        plan.build_templates()
+        Z, V, G = plan.n_z, plan.valid, plan.group_segments
+        full = torch.empty((Z, n_bins), dtype=torch.float32, device="cuda")
+        plan.convolve_power(spec, full)
+        plan.check()
+        n_groups = -(-plan.n_seg // G)
+        rng = np.random.default_rng(82)
+        keep = rng.random(n_groups * Z) < 0.3
+        keep[0] = keep[-1] = True
+        units = np.flatnonzero(keep).astype(np.int32)
+        masks = rng.integers(1, 1 << G, units.size).astype(np.uint16)
+        masks[: min(8, masks.size)] = [1 << (j % G) for j in range(min(8, masks.size))]
+        masks[-1] = (1 << G) - 1
+        part = torch.full((Z, n_bins), float("nan"), dtype=torch.float32, device="cuda")
+        d_masks = torch.from_numpy(masks.view(np.int16).copy()).cuda()
+        plan.convolve_power_units(spec, part, dev(units), units.size, masks=d_masks)
+        plan.check()
+        f, p = full.cpu().numpy(), part.cpu().numpy()
+    on = np.zeros((Z, n_bins), dtype=bool)
+    for u, mk in zip(units, masks):
+        g, z = divmod(int(u), Z)
+        for j in range(G):
+            if (int(mk) >> j) & 1:
+                on[z, (g * G + j) * V:(g * G + j + 1) * V] = True
+    np.testing.assert_array_equal(p[on], f[on])
+    assert np.all(np.isnan(p[~on]))
+
+
+@pytest.mark.parametrize("nw,Z,G,n_groups", [(400, 21, 8, 17), (300, 300, 4, 25)])
+def test_masked_work_units_match_oracle(nw, Z, G, n_groups):
+    """Units and segment masks against the oracle's definition (exact)."""
+    rng = np.random.default_rng(91 + nw)
+    thr = 0.3
+    logits = rng.normal(-3.0, 2.0, (nw, Z)).astype(np.float32)
+    lthr = np.log(thr / (1 - thr))
+    logits[np.abs(logits - lthr) < 1e-3] += 0.01
+    hop, V, h = 512, 1536, 256
+    units = torch.full((n_groups * Z,), -1, dtype=torch.int32, device="cuda")
+    masks = torch.zeros((n_groups * Z,), dtype=torch.int16, device="cuda")
+    n = fdas.zband_work_units(dev(logits), nw, Z, thr, hop, G * V, h, n_groups, units, masks=masks, segments=G)
+    want_u, want_m = oz.work_unit_masks(logits.astype(np.float64), thr, hop, V, G, h, n_groups)
+    assert n == want_u.size
+    np.testing.assert_array_equal(units[:n].cpu().numpy(), want_u)
+    np.testing.assert_array_equal(masks[:n].cpu().numpy().view(np.uint16), want_m)

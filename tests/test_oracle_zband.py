@@ -171,3 +171,20 @@ def test_work_units_hand_computed():
     np.testing.assert_array_equal(got, [0 * 2 + 0, 1 * 2 + 1, 2 * 2 + 1])
     assert zband.work_units(np.full((4, 2), lo), 0.5, 4, 5, 1, 3).size == 0
     np.testing.assert_array_equal(zband.work_units(np.full((4, 2), hi), 0.5, 4, 5, 1, 3), np.arange(6))
+
+
+def test_work_unit_masks_hand_case_and_group_flags():
+    """Masks on a hand-computed case, and one segment per group reproduces work_units."""
+    # blocks of hop 4; two groups of two 3-bin segments, h = 1: segment s draws on [3s - 1, 3s + 4)
+    logits = np.full((4, 2), -10.0)
+    logits[1, 0] = 10.0          # block 1 = bins [4, 8): segments 1 ([2, 7)) and 2 ([5, 10))
+    logits[3, 1] = 10.0          # block 3 = bins [12, 16): segment 3 ([8, 13)) only
+    units, masks = zband.work_unit_masks(logits, 0.5, 4, 3, 2, 1, 2)
+    # group 0 = segments 0, 1; group 1 = segments 2, 3
+    assert list(units) == [0, 2, 3] and list(masks) == [0b10, 0b01, 0b10]
+    rng = np.random.default_rng(8)
+    lg = rng.normal(-2.0, 2.0, (30, 5))
+    u1 = zband.work_units(lg, 0.3, 512, 1536 * 8, 256, 4)
+    u2, m2 = zband.work_unit_masks(lg, 0.3, 512, 1536 * 8, 1, 256, 4)
+    np.testing.assert_array_equal(u1, u2)
+    assert np.all(m2 == 1)
