@@ -160,7 +160,8 @@ int fdas_check(fdas_plan* plan, fdas_stream_t stream);
  */
 int fdas_selftest_wait_timeout(fdas_plan* plan, int64_t limit_ns, fdas_stream_t stream);
 
-/* Free the plan's device memory (synchronises the device first).  NULL is a no-op. */
+/* Free the plan's device memory.  Waits first for the last work the plan enqueued (not for the whole
+ * device: work of other plans and other streams keeps running).  NULL is a no-op. */
 int fdas_destroy(fdas_plan* plan);
 
 /* Plan sizes: Z templates, V valid outputs per segment, nseg = ceil(n_bins / V) segments.
@@ -377,16 +378,36 @@ int fdas_zband_destroy(fdas_zband* net);
  * Asynchronous on `stream`.  The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.  The template bank is
  * rebuilt (FP64, tens of ms for the survey geometry) whenever (zmax, zstep, seg_len, tmpl_len)
- * differs from the previous call on the same device, and reused otherwise; the status word is
- * cleared on every call.  All calls share the one array, which keeps the last call's contents:
- * calls that overlap on the GPU (other streams, other host threads without ordering) race.  A
- * bounded device wait that gives up leaves the plane unspecified and is recorded only in the
- * array's status word, which this call does not read back.  Returns FDAS_OK, FDAS_ERR_INVALID,
- * FDAS_ERR_ALIGN, FDAS_ERR_NO_DEVICE, FDAS_ERR_UNSUPPORTED or FDAS_ERR_CUDA.
+ * differs from the previous call on the same device, and reused otherwise.  A call that finds the
+ * bank already built still depends on the stream of the call that built it: order the first call
+ * before calls on other streams.  All calls share the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host threads without ordering)
+ * race.  A bounded device wait that gives up leaves the plane unspecified and sets the array's
+ * status word, which accumulates over calls until fdas_static_check reads and clears it.  Returns
+ * FDAS_OK, FDAS_ERR_INVALID, FDAS_ERR_ALIGN, FDAS_ERR_NO_DEVICE, FDAS_ERR_UNSUPPORTED or
+ * FDAS_ERR_CUDA.
  */
 #define FDAS_STATIC_SCRATCH_BYTES (8u << 20)
 int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len,
                                const float* d_spectrum, float* d_plane, fdas_stream_t stream);
+
+/*
+ * Status of the allocation-free calls on the current device (the paper has no counterpart; this is
+ * the static array's analogue of fdas_check).  Synchronises `stream`, reads the status word kept in
+ * the static array, clears it and returns FDAS_ERR_TIMEOUT if a bounded device wait of any
+ * fdas_convolve_power_static call since the last check gave up (those planes are unspecified),
+ * FDAS_OK otherwise, FDAS_ERR_CUDA on a runtime error.  Allocates nothing.
+ */
+int fdas_static_check(fdas_stream_t stream);
+
+/*
+ * Failure-detection self test of the static array's status word (no counterpart in the paper): as
+ * fdas_selftest_wait_timeout, one thread waits at most limit_ns (1 us .. 2 s) on a barrier nothing
+ * completes and records the timeout in the static array's status word; the next
+ * fdas_static_check returns FDAS_ERR_TIMEOUT.  Asynchronous on `stream`; FDAS_ERR_INVALID for a
+ * limit out of range.  Allocates nothing.
+ */
+int fdas_static_selftest_wait_timeout(int64_t limit_ns, fdas_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -33,6 +33,9 @@ struct fdas_plan {
   unsigned char* tc_mats = nullptr;  // DFT matrices, BF16 then FP16
   unsigned* tc_tmax = nullptr;
   bool tc_ready = false;
+  // completion of the last work this plan enqueued (fdas_destroy and the introspection calls wait
+  // on it instead of on the whole device)
+  cudaEvent_t done = nullptr;
 };
 
 namespace {
@@ -66,6 +69,17 @@ void gauss_legendre(int n, double* x, double* w) {
     x[i] = z;
     w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
   }
+}
+
+// The quadrature rule, computed once per process (a function-local static is initialised
+// exactly once even when several host threads build plans at the same time).
+struct GLTable {
+  double x[kGLPoints], w[kGLPoints];
+  GLTable() { gauss_legendre(kGLPoints, x, w); }
+};
+const GLTable& gl_table() {
+  static const GLTable table;
+  return table;
 }
 
 // a1, part 1: raw response H_q(z) = int_0^1 exp(i pi (z u^2 - (z+2q) u)) du by composite
@@ -185,7 +199,7 @@ __global__ void wait_selftest_kernel(int* status, unsigned long long limit_ns) {
   __shared__ uint64_t bar;
   fdas::mbar_init(&bar, 1);
   fdas::fence_barrier_init();
-  if (!fdas::mbar_wait(&bar, 0, limit_ns)) atomicOr(status, 1);
+  if (!fdas::mbar_wait(&bar, 0, limit_ns)) atomicOr(status, fdas::kStatusTimeout);
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
@@ -203,18 +217,31 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+EncodeTiledFn lookup_encode_fn() {
+  void* ptr = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<EncodeTiledFn>(ptr);
+}
 EncodeTiledFn get_encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return nullptr;
-    fn = reinterpret_cast<EncodeTiledFn>(ptr);
-  }
+  static const EncodeTiledFn fn = lookup_encode_fn();   // looked up once, thread-safe
   return fn;
+}
+
+// Record the plan's completion event after work enqueued on `st` (skipped while the stream is
+// being captured into a CUDA graph: a captured record is not an event the host can wait on).
+int note_work(fdas_plan* p, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return FDAS_OK;
+  return cudaEventRecord(p->done, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+int enqueued(fdas_plan* p, cudaStream_t st, cudaError_t launch) {
+  if (launch != cudaSuccess) return FDAS_ERR_CUDA;
+  return note_work(p, st);
 }
 
 // 1-D tensor map over the spectrum: n_bins elements of 8 bytes, box of min(L, 256) elements,
@@ -253,6 +280,8 @@ void free_tc_memory(fdas_plan* p) {
 
 void free_plan_memory(fdas_plan* p) {
   free_tc_memory(p);
+  if (p->done) cudaEventDestroy(p->done);
+  p->done = nullptr;
   cudaFree(p->d_templates);
   cudaFree(p->d_taps);
   cudaFree(p->d_twist);
@@ -330,7 +359,8 @@ fdas_plan* fdas_plan_create(int64_t n_bins, int zmax, int zstep, int seg_len, in
   if (cudaMalloc(&p->d_templates, sizeof(float2) * (size_t)p->Z * p->L) != cudaSuccess ||
       cudaMalloc(&p->d_taps, sizeof(double2) * (size_t)p->Z * ntap) != cudaSuccess ||
       cudaMalloc(&p->d_twist, sizeof(float2) * (size_t)p->L) != cudaSuccess ||
-      cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     free_plan_memory(p);
     delete p;
@@ -348,26 +378,13 @@ fdas_plan* fdas_plan_create(int64_t n_bins, int zmax, int zstep, int seg_len, in
 
 int fdas_templates_build(fdas_plan* p, fdas_stream_t stream) {
   if (!p) return FDAS_ERR_INVALID;
-  static bool gl_ready = false;
-  static double gl_x[kGLPoints], gl_w[kGLPoints];
-  if (!gl_ready) {
-    gauss_legendre(kGLPoints, gl_x, gl_w);
-    gl_ready = true;
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(gl_x), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(gl_w), 0, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (fdas::build_templates_into(p->d_taps, p->d_templates, p->d_twist, p->zmax, p->zstep, p->L, p->m, st) !=
+      cudaSuccess)
     return FDAS_ERR_CUDA;
-  taps_kernel<<<p->Z, 256, 0, st>>>(p->d_taps, p->zmax, p->zstep, p->h);
-  const size_t tab = sizeof(double2) * (size_t)p->L;
-  if (cudaFuncSetAttribute(spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab) != cudaSuccess)
-    return FDAS_ERR_CUDA;
-  spectra_kernel<<<dim3((p->L + 255) / 256, p->Z), 256, tab, st>>>(p->d_taps, p->d_templates, p->L, p->h, p->n1);
-  twist_kernel<<<(p->L + 255) / 256, 256, 0, st>>>(p->d_twist, p->L, p->n1);
-  if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;
   p->built = true;
   p->tc_ready = false;   // the tensor-core variant copies the bank again on its next call
-  return FDAS_OK;
+  return note_work(p, st);
 }
 
 int fdas_convolve_power(fdas_plan* p, const float* d_spectrum, float* d_plane, fdas_stream_t stream) {
@@ -389,8 +406,8 @@ int fdas_convolve_power(fdas_plan* p, const float* d_spectrum, float* d_plane, f
   q.Z = p->Z;
   q.V = p->V;
   q.h = p->h;
-  cudaError_t e = fdas::launch_convolve(p->L, &p->map, q, p->sm_count, reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_convolve(p->L, &p->map, q, p->sm_count, st));
 }
 
 int fdas_plan_group_segments(const fdas_plan* p) {
@@ -420,9 +437,8 @@ int fdas_convolve_power_units_masked(fdas_plan* p, const float* d_spectrum, floa
   q.Z = p->Z;
   q.V = p->V;
   q.h = p->h;
-  cudaError_t e = fdas::launch_units(p->L, q, d_units, d_masks, n_units, p->sm_count,
-                                     reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_units(p->L, q, d_units, d_masks, n_units, p->sm_count, st));
 }
 
 int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_units,
@@ -446,9 +462,8 @@ int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fd
   q.nseg = p->nseg;
   q.V = p->V;
   q.h = p->h;
-  cudaError_t e =
-      fdas::launch_segment_spectra(p->L, &p->map, q, p->sm_count, reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_segment_spectra(p->L, &p->map, q, p->sm_count, st));
 }
 
 namespace {
@@ -515,7 +530,7 @@ int fdas_convolve_power_tc(fdas_plan* p, const float* d_spectrum, float* d_plane
     return FDAS_ERR_CUDA;
   fdas::TcParams q = tc_params(p, d_spectrum, precision, false);
   q.plane = d_plane;
-  return fdas::launch_tc(q, precision, false, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return enqueued(p, st, fdas::launch_tc(q, precision, false, p->sm_count, st));
 }
 
 int fdas_segment_spectra_tc(fdas_plan* p, const float* d_spectrum, float* d_out, int precision,
@@ -526,7 +541,7 @@ int fdas_segment_spectra_tc(fdas_plan* p, const float* d_spectrum, float* d_out,
   if ((rc = tc_ensure_ready(p, st)) != FDAS_OK) return rc;
   fdas::TcParams q = tc_params(p, d_spectrum, precision, true);
   q.seg_out = reinterpret_cast<float2*>(d_out);
-  return fdas::launch_tc(q, precision, true, p->sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return enqueued(p, st, fdas::launch_tc(q, precision, true, p->sm_count, st));
 }
 
 int fdas_check(fdas_plan* p, fdas_stream_t stream) {
@@ -536,21 +551,20 @@ int fdas_check(fdas_plan* p, fdas_stream_t stream) {
   if (cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
   if (status != 0) {
     cudaMemset(p->d_status, 0, sizeof(int));
-    return (status & 1) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
+    return (status & fdas::kStatusTimeout) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
   }
   return FDAS_OK;
 }
 
 int fdas_selftest_wait_timeout(fdas_plan* p, int64_t limit_ns, fdas_stream_t stream) {
   if (!p || limit_ns < 1000 || limit_ns > 2000000000LL) return FDAS_ERR_INVALID;
-  wait_selftest_kernel<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p->d_status,
-                                                                             (unsigned long long)limit_ns);
-  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_wait_selftest(p->d_status, limit_ns, st));
 }
 
 int fdas_destroy(fdas_plan* p) {
   if (!p) return FDAS_OK;
-  cudaDeviceSynchronize();
+  if (p->done) cudaEventSynchronize(p->done);   // the plan's last enqueued work, not the whole device
   free_plan_memory(p);
   delete p;
   return FDAS_OK;
@@ -568,7 +582,7 @@ int fdas_template_taps(fdas_plan* p, int z_idx, double* host_out) {
   if (!p || !host_out || z_idx < 0 || z_idx >= p->Z) return FDAS_ERR_INVALID;
   if (!p->built) return FDAS_ERR_NOT_BUILT;
   const size_t ntap = (size_t)p->m + 1;
-  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaEventSynchronize(p->done) != cudaSuccess) return FDAS_ERR_CUDA;
   if (cudaMemcpy(host_out, p->d_taps + (size_t)z_idx * ntap, sizeof(double2) * ntap, cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return FDAS_ERR_CUDA;
@@ -578,7 +592,7 @@ int fdas_template_taps(fdas_plan* p, int z_idx, double* host_out) {
 int fdas_template_spectrum(fdas_plan* p, int z_idx, float* host_out) {
   if (!p || !host_out || z_idx < 0 || z_idx >= p->Z) return FDAS_ERR_INVALID;
   if (!p->built) return FDAS_ERR_NOT_BUILT;
-  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaEventSynchronize(p->done) != cudaSuccess) return FDAS_ERR_CUDA;
   float2* tmp = static_cast<float2*>(std::malloc(sizeof(float2) * (size_t)p->L));
   if (!tmp) return FDAS_ERR_ALLOC;
   if (cudaMemcpy(tmp, p->d_templates + (size_t)z_idx * p->L, sizeof(float2) * (size_t)p->L,
@@ -610,14 +624,9 @@ int validate_geometry(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl
 
 cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist, int zmax, int zstep, int L,
                                  int m, cudaStream_t st) {
-  static bool gl_ready = false;
-  static double gl_x[kGLPoints], gl_w[kGLPoints];
-  if (!gl_ready) {
-    gauss_legendre(kGLPoints, gl_x, gl_w);
-    gl_ready = true;
-  }
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl_x, sizeof(gl_x), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gl_w, gl_w, sizeof(gl_w), 0, cudaMemcpyHostToDevice, st);
+  const GLTable& gl = gl_table();
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, gl.x, sizeof(gl.x), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gl_w, gl.w, sizeof(gl.w), 0, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   const int Z = 2 * (zmax / zstep) + 1, h = m / 2, n1 = conv_group_threads(L);
   taps_kernel<<<Z, 256, 0, st>>>(taps, zmax, zstep, h);
@@ -626,6 +635,11 @@ cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist
   if (e != cudaSuccess) return e;
   spectra_kernel<<<dim3((L + 255) / 256, Z), 256, tab, st>>>(taps, templates, L, h, n1);
   twist_kernel<<<(L + 255) / 256, 256, 0, st>>>(twist, L, n1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int* status, int64_t limit_ns, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 1, 0, st>>>(status, (unsigned long long)limit_ns);
   return cudaGetLastError();
 }
 

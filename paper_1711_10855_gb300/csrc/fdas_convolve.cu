@@ -181,10 +181,28 @@ __device__ __forceinline__ void store_spectrum_element(float* sx, int t, int k2,
   sx[base + 2] = im;
 }
 
-// Device status word: set bit 0 when a bounded wait gave up.
+// One arrival on a shared-memory consumer counter with acquire-release semantics at CTA scope: the
+// caller's earlier reads of the slot (ordered within the warp by __syncwarp) happen before the
+// arrival, and the last arriver's later refill of the slot happens after every other arrival.
+// Returns the count before this arrival.
+__device__ __forceinline__ unsigned arrive_count(unsigned* counter) {
+  unsigned old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(smem_u32(counter)) : "memory");
+  return old;
+}
+
+// Bounded wait for a template slot: the common case (already filled) costs one try_wait; the abort
+// flag is read only when the slot is not ready, so one warp's timeout stops the others quickly.
+__device__ __forceinline__ int wait_slot(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return 1;
+  if (*abort_flag) return 0;
+  return mbar_wait(bar, parity) ? 1 : 0;
+}
+
+// Device status word: set kStatusTimeout when a bounded wait gave up.
 __device__ __forceinline__ void report_timeout(int* status, volatile int* abort_flag) {
   *abort_flag = 1;
-  atomicOr(status, 1);
+  atomicOr(status, kStatusTimeout);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -294,8 +312,7 @@ __global__ void __launch_bounds__(256, 1)
     for (; i < b; i += P) {
       const int slot = (int)(i % R);
       // warp-uniform bounded wait for the template of position i
-      int ok = *abort_flag ? 0 : (mbar_wait(&full[slot], (uint32_t)((i / R) & 1)) ? 1 : 0);
-      ok = __all_sync(0xffffffffu, ok);
+      const int ok = __all_sync(0xffffffffu, wait_slot(&full[slot], (uint32_t)((i / R) & 1), abort_flag));
       if (!ok) {
         if (lane == 0) report_timeout(p.status, abort_flag);
         break;
@@ -314,10 +331,8 @@ __global__ void __launch_bounds__(256, 1)
       // release the template slot; the last of the W/P consumers refills it R positions ahead
       __syncwarp();
       if (lane == 0) {
-        __threadfence_block();
-        const unsigned old = atomicAdd(&cnt[slot], 1u);
+        const unsigned old = arrive_count(&cnt[slot]);
         if ((old + 1u) % (unsigned)(Cfg::W / P) == 0u) {
-          __threadfence_block();
           if (i + R < npos) {
             fence_proxy_async_smem();
             issue_template(i + R);
@@ -452,9 +467,9 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   const int64_t u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
   const int64_t npos = u1 - u0;
   if (npos <= 0) return;
-  // a work list that failed its check (status bit 2, set by the preceding check kernel) is not run
+  // a work list that failed its check (kStatusBadList, set by the preceding check kernel) is not run
   if constexpr (LIST) {
-    if (*reinterpret_cast<volatile const int*>(p.status) & 2) return;
+    if (*reinterpret_cast<volatile const int*>(p.status) & kStatusBadList) return;
   }
 
   if (tid == 0) {
@@ -537,10 +552,8 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   auto release_slot = [&](int64_t i, int slot) {
     __syncwarp();
     if (lane == 0) {
-      __threadfence_block();
-      const unsigned old = atomicAdd(&cnt[slot], 1u);
+      const unsigned old = arrive_count(&cnt[slot]);
       if ((old + 1u) % (unsigned)W == 0u) {
-        __threadfence_block();
         if (i + R < npos) {
           fence_proxy_async_smem();
           issue_template(i + R);
@@ -631,8 +644,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     const int lim = lim64 > 0 ? (int)lim64 : 0;
     for (int64_t i = a; i < bpos; ++i) {
       const int slot = (int)(i % R);
-      int ok = *abort_flag ? 0 : (mbar_wait(&full[slot], (uint32_t)((i / R) & 1)) ? 1 : 0);
-      ok = __all_sync(0xffffffffu, ok);
+      const int ok = __all_sync(0xffffffffu, wait_slot(&full[slot], (uint32_t)((i / R) & 1), abort_flag));
       if (!ok) {
         if (lane == 0) report_timeout(p.status, abort_flag);
         break;
@@ -744,7 +756,7 @@ __global__ void __launch_bounds__(256, 1)
   const int ok = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0);
   if (!ok) {
     if (tid == 0) {
-      atomicOr(p.status, 1);
+      atomicOr(p.status, kStatusTimeout);
       (void)mbar_wait(bar, 0);   // bounded wait for copies still in flight
     }
     return;
@@ -859,11 +871,11 @@ static cudaError_t launch_single_desc(int L, const ConvParams& p, int sm_count, 
 }
 
 // A work list is usable when its entries are strictly increasing and inside [0, limit): that
-// bounds every template row, segment and plane row the kernel touches.  Otherwise status bit 2.
+// bounds every template row, segment and plane row the kernel touches.  Otherwise kStatusBadList.
 __global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limit, int* status) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = units[e];
-    if (u < 0 || u >= limit || (e > 0 && (int64_t)units[e - 1] >= u)) atomicOr(status, 2);
+    if (u < 0 || u >= limit || (e > 0 && (int64_t)units[e - 1] >= u)) atomicOr(status, kStatusBadList);
   }
 }
 

@@ -8,13 +8,17 @@
 
 namespace fdas {
 
+// Bits of a device status word.
+constexpr int kStatusTimeout = 1;   // a bounded device wait gave up
+constexpr int kStatusBadList = 2;   // a work list failed its check and was not run
+
 // Parameters of the fused correlation kernel (steps a2..a7).
 struct ConvParams {
   const float2* spectrum;   // n_bins complex64 (read by bulk copies in the descriptor-driven kernel)
   const float2* templates;  // Z x L template spectra, per-template layout of the IFFT's first pass
   const float2* twist;      // L inter-pass twiddles exp(+i 2pi n2 k1 / L), same layout
   float* plane;             // Z x n_bins output, row pitch n_bins
-  int* status;              // device status word (bit 0: a bounded wait gave up; bit 1: bad work list)
+  int* status;              // device status word (kStatusTimeout | kStatusBadList)
   int64_t n_bins;
   int64_t nseg;             // ceil(n_bins / V)
   int64_t units;            // (number of segment groups) x Z
@@ -37,7 +41,7 @@ struct SpecDesc {
 struct BatchParams {
   const float2* templates;  // Z_bank x L template spectra (pair-major layout)
   const float2* twist;      // L inter-pass twiddles (pair-major layout)
-  int* status;              // device status word (bit 0: a bounded wait gave up; bit 1: bad work list)
+  int* status;              // device status word (kStatusTimeout | kStatusBadList)
   const SpecDesc* descs;    // device table of `count` spectra, or nullptr: use `single`
   SpecDesc single;
   int count;
@@ -115,4 +119,6 @@ int validate_geometry(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl
 cudaError_t build_templates_into(double2* taps, float2* templates, float2* twist, int zmax, int zstep, int L,
                                  int m, cudaStream_t st);
 int encode_spectrum_map(CUtensorMap* map, const void* d_spectrum, int64_t n_bins, int L);
+// One thread waits, for at most limit_ns, on a barrier nothing completes and sets kStatusTimeout.
+cudaError_t launch_wait_selftest(int* status, int64_t limit_ns, cudaStream_t st);
 }  // namespace fdas

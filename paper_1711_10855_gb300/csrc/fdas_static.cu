@@ -1,6 +1,7 @@
 // fdas_static.cu -- fdas_convolve_power_static: the fused correlation without any device
 // allocation (declared in include/fdas.h).  The template bank, FP64 taps, twiddle table and
-// status word live in one file-scope device array instead of plan memory.
+// status word live in one file-scope device array instead of plan memory; fdas_static_check
+// reads (and clears) that status word, fdas_static_selftest_wait_timeout exercises it.
 #include <cstdint>
 #include <mutex>
 
@@ -31,40 +32,21 @@ std::mutex g_mutex;
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
-}  // namespace
-
-extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len,
-                                          const float* d_spectrum, float* d_plane, fdas_stream_t stream) {
-  int rc = fdas::validate_geometry(n_bins, zmax, zstep, seg_len, tmpl_len);
-  if (rc != FDAS_OK) return rc;
-  const int L = seg_len, m = tmpl_len, h = m / 2, V = L - m;
-  const int Z = 2 * (zmax / zstep) + 1;
-  // layout inside the array: template spectra | taps | twiddles | status word
-  const size_t off_tmpl = 0;
-  const size_t off_taps = off_tmpl + round256(sizeof(float2) * (size_t)Z * L);
-  const size_t off_twist = off_taps + round256(sizeof(double2) * (size_t)Z * (m + 1));
-  const size_t off_status = off_twist + round256(sizeof(float2) * (size_t)L);
-  const size_t need = off_status + 256;
-  if (need > (size_t)FDAS_STATIC_SCRATCH_BYTES) return FDAS_ERR_INVALID;
-  if (!d_spectrum || !d_plane) return FDAS_ERR_INVALID;
-  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u))
-    return FDAS_ERR_ALIGN;
-
+// The array's device address on the current device, looked up once per device (with that device
+// current), and the device's SM count.  Returns FDAS_OK or an error code; g_mutex must be held.
+int device_scratch(DeviceScratch** out) {
   int ndev = 0, dev = 0, major = 0, minor = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
     return FDAS_ERR_NO_DEVICE;
   }
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDAS_ERR_CUDA;
-  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
-    return FDAS_ERR_CUDA;
-  if (major != 10 || minor != 3) return FDAS_ERR_UNSUPPORTED;
-
-  std::lock_guard<std::mutex> lock(g_mutex);
   DeviceScratch& s = g_dev[dev];
   if (!s.ready) {
-    // once per device, with that device current: the array's device address
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+      return FDAS_ERR_CUDA;
+    if (major != 10 || minor != 3) return FDAS_ERR_UNSUPPORTED;
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr) {
       cudaGetLastError();
@@ -76,11 +58,41 @@ extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, i
     s.sm_count = sms;
     s.ready = true;
   }
+  *out = &s;
+  return FDAS_OK;
+}
+
+// Layout of the array: status word (its own 256 bytes, at a fixed place so that it survives
+// calls with other geometries) | template spectra | taps | twiddles.
+constexpr size_t kOffStatus = 0;
+constexpr size_t kOffBank = 256;
+
+}  // namespace
+
+extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, int seg_len, int tmpl_len,
+                                          const float* d_spectrum, float* d_plane, fdas_stream_t stream) {
+  int rc = fdas::validate_geometry(n_bins, zmax, zstep, seg_len, tmpl_len);
+  if (rc != FDAS_OK) return rc;
+  const int L = seg_len, m = tmpl_len, h = m / 2, V = L - m;
+  const int Z = 2 * (zmax / zstep) + 1;
+  const size_t off_tmpl = kOffBank;
+  const size_t off_taps = off_tmpl + round256(sizeof(float2) * (size_t)Z * L);
+  const size_t off_twist = off_taps + round256(sizeof(double2) * (size_t)Z * (m + 1));
+  const size_t need = off_twist + round256(sizeof(float2) * (size_t)L);
+  if (need > (size_t)FDAS_STATIC_SCRATCH_BYTES) return FDAS_ERR_INVALID;
+  if (!d_spectrum || !d_plane) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u))
+    return FDAS_ERR_ALIGN;
+
+  std::lock_guard<std::mutex> lock(g_mutex);
+  DeviceScratch* sp = nullptr;
+  if ((rc = device_scratch(&sp)) != FDAS_OK) return rc;
+  DeviceScratch& s = *sp;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   float2* templates = reinterpret_cast<float2*>(s.base + off_tmpl);
   double2* taps = reinterpret_cast<double2*>(s.base + off_taps);
   float2* twist = reinterpret_cast<float2*>(s.base + off_twist);
-  int* status = reinterpret_cast<int*>(s.base + off_status);
+  int* status = reinterpret_cast<int*>(s.base + kOffStatus);
 
   if (!s.have_bank || s.zmax != zmax || s.zstep != zstep || s.L != L || s.m != m) {
     s.have_bank = false;
@@ -92,7 +104,6 @@ extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, i
     s.L = L;
     s.m = m;
   }
-  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return FDAS_ERR_CUDA;
 
   CUtensorMap map;
   rc = fdas::encode_spectrum_map(&map, d_spectrum, n_bins, L);
@@ -110,4 +121,30 @@ extern "C" int fdas_convolve_power_static(int64_t n_bins, int zmax, int zstep, i
   q.V = V;
   q.h = h;
   return fdas::launch_convolve(L, &map, q, s.sm_count, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+extern "C" int fdas_static_check(fdas_stream_t stream) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  DeviceScratch* sp = nullptr;
+  int rc = device_scratch(&sp);
+  if (rc != FDAS_OK) return rc;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  int* status = reinterpret_cast<int*>(sp->base + kOffStatus);
+  int word = 0;
+  if (cudaMemcpy(&word, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (word == 0) return FDAS_OK;
+  if (cudaMemset(status, 0, sizeof(int)) != cudaSuccess) return FDAS_ERR_CUDA;
+  return (word & fdas::kStatusTimeout) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
+}
+
+extern "C" int fdas_static_selftest_wait_timeout(int64_t limit_ns, fdas_stream_t stream) {
+  if (limit_ns < 1000 || limit_ns > 2000000000LL) return FDAS_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  DeviceScratch* sp = nullptr;
+  int rc = device_scratch(&sp);
+  if (rc != FDAS_OK) return rc;
+  int* status = reinterpret_cast<int*>(sp->base + kOffStatus);
+  return fdas::launch_wait_selftest(status, limit_ns, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? FDAS_OK
+             : FDAS_ERR_CUDA;
 }

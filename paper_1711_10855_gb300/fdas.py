@@ -35,7 +35,8 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_zband_predict", "fdas_zband_propose", "fdas_zband_check", "fdas_zband_spectrum_windows",
             "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc",
             "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes",
-            "fdas_convolve_power_units_masked", "fdas_zband_work_units_masked"]
+            "fdas_convolve_power_units_masked", "fdas_zband_work_units_masked",
+            "fdas_static_check", "fdas_static_selftest_wait_timeout"]
 
 _lock = threading.Lock()
 _lib = None
@@ -142,6 +143,10 @@ def lib() -> ctypes.CDLL:
             L.fdas_selftest_wait_timeout.restype = i32
             L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
             L.fdas_convolve_power_static.restype = i32
+            L.fdas_static_check.argtypes = [vp]
+            L.fdas_static_check.restype = i32
+            L.fdas_static_selftest_wait_timeout.argtypes = [i64, vp]
+            L.fdas_static_selftest_wait_timeout.restype = i32
             _lib = L
     return _lib
 
@@ -503,6 +508,12 @@ def convolve_power_static(n_bins: int, zmax: int, zstep: int, seg_len: int, tmpl
     _check(lib().fdas_convolve_power_static(int(n_bins), int(zmax), int(zstep), int(seg_len), int(tmpl_len),
                                             _ptr(spectrum), _ptr(plane), _stream(stream)),
            "fdas_convolve_power_static")
+
+
+def static_check(stream=None):
+    """fdas_static_check: raise FdasError if a bounded device wait of an allocation-free call gave up
+    since the last check (the status word is cleared either way)."""
+    _check(lib().fdas_static_check(_stream(stream)), "fdas_static_check")
 
 
 def plane_shape(plan: Plan) -> tuple[int, int]:

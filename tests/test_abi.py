@@ -78,6 +78,14 @@ def test_null_plan_calls(lib):
     assert lib.fdas_template_spectrum(None, 0, None) == -1
     assert lib.fdas_segment_spectra(None, None, None, None) == -1
     assert lib.fdas_selftest_wait_timeout(None, ctypes.c_int64(1000000), None) == -1
+    assert lib.fdas_static_selftest_wait_timeout(ctypes.c_int64(0), None) == -1
+
+
+def test_static_check_without_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    assert lib.fdas_static_check(None) == fdas.FDAS_ERR_NO_DEVICE
 
 
 def test_no_device_is_an_error_not_a_fallback(lib, cuda_available):
