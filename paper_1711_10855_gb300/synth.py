@@ -105,3 +105,39 @@ def survey() -> Workload:
 def with_seg_len(w: Workload, seg_len: int) -> Workload:
     return Workload(w.name + f"-L{seg_len}", w.n_samples, w.zmax, w.zstep, w.tmpl_len, seg_len,
                     w.seed, w.chirps)
+
+
+def batch_workload(count: int, seed: int = 171110857):
+    """De-dispersion-trial batch geometry: n_bins log-uniform in [2^18, 2^22] (multiples of 4),
+    zmax 100 or 200 (step 2) per spectrum, 512-tap templates."""
+    rng = np.random.default_rng(seed)
+    n = (np.exp(rng.uniform(np.log(2 ** 18), np.log(2 ** 22), count)).astype(np.int64) // 4) * 4
+    zmax = rng.choice([100, 200], count).astype(np.int32)
+    return n, zmax
+
+
+def batch_spectra(torch, n_bins, zmax, m: int, dev, seed: int = 171110858):
+    """Batch inputs on the device: for spectrum i, 2*n_bins[i] unit Gaussian samples plus 0-4
+    chirps (r0 uniform in [m, n-m-200], z uniform in [-0.9 zmax_i, 0.9 zmax_i], amplitude uniform in
+    [0.01, 0.05]), phases in FP64, real FFT with the Nyquist bin dropped, complex64 (interleaved
+    float32 tensors).  Returns the spectra and, per spectrum, its tuple of Chirps."""
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    specs, chirps = [], []
+    for n, zm in zip(n_bins, zmax):
+        N = 2 * int(n)
+        x = torch.randn(N, generator=gen, device=dev, dtype=torch.float64)
+        u = torch.arange(N, device=dev, dtype=torch.float64) / N
+        cs = []
+        for _ in range(int(rng.integers(0, 5))):
+            r0 = rng.uniform(m, int(n) - m - 200)
+            z = rng.uniform(-0.9 * zm, 0.9 * zm)
+            a = rng.uniform(0.01, 0.05)
+            ph = rng.uniform(0, 2 * np.pi)
+            x += a * torch.cos(2 * np.pi * (r0 * u + 0.5 * z * u * u) + ph)
+            cs.append(Chirp(float(r0), float(z), float(a), float(ph)))
+        specs.append(torch.view_as_real(torch.fft.rfft(x)[: int(n)].to(torch.complex64)).reshape(-1).contiguous())
+        chirps.append(tuple(cs))
+        del x, u
+    return specs, chirps

@@ -52,11 +52,11 @@ def test_algorithmic_counts_of_the_survey_plane():
 
 
 def test_batch_workload_shape():
-    n, zmax = bench.batch_workload(256)
+    n, zmax = synth.batch_workload(256)
     assert n.size == zmax.size == 256
     assert np.all(n % 4 == 0) and n.min() >= (1 << 18) - 4 and n.max() <= 1 << 22
     assert set(np.unique(zmax)) <= {100, 200}
-    n2, z2 = bench.batch_workload(256)
+    n2, z2 = synth.batch_workload(256)
     np.testing.assert_array_equal(n, n2)
     np.testing.assert_array_equal(zmax, z2)
 
