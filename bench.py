@@ -226,37 +226,6 @@ def run_reference(args):
     return 0
 
 
-def batch_workload(count: int, seed: int = 171110857):
-    """256 de-dispersion-trial spectra: n_bins log-uniform in [2^18, 2^22] (multiples of 4), zmax
-    100 or 200 (step 2) per spectrum, 512-tap templates."""
-    rng = np.random.default_rng(seed)
-    n = (np.exp(rng.uniform(np.log(2 ** 18), np.log(2 ** 22), count)).astype(np.int64) // 4) * 4
-    zmax = rng.choice([100, 200], count).astype(np.int32)
-    return n, zmax
-
-
-def batch_spectra(torch, n_bins, zmax, m: int, dev, seed: int = 171110858):
-    """Batch inputs on the device: for spectrum i, 2*n_bins[i] unit Gaussian samples plus 0-4
-    chirps (r0 uniform in [m, n-m-200], z uniform in [-0.9 zmax_i, 0.9 zmax_i], amplitude uniform in
-    [0.01, 0.05]), phases in FP64, real FFT with the Nyquist bin dropped, complex64."""
-    rng = np.random.default_rng(seed)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(seed)
-    specs = []
-    for n, zm in zip(n_bins, zmax):
-        N = 2 * int(n)
-        x = torch.randn(N, generator=gen, device=dev, dtype=torch.float64)
-        u = torch.arange(N, device=dev, dtype=torch.float64) / N
-        for _ in range(int(rng.integers(0, 5))):
-            r0 = rng.uniform(m, int(n) - m - 200)
-            z = rng.uniform(-0.9 * zm, 0.9 * zm)
-            a = rng.uniform(0.01, 0.05)
-            x += a * torch.cos(2 * np.pi * (r0 * u + 0.5 * z * u * u) + rng.uniform(0, 2 * np.pi))
-        specs.append(torch.view_as_real(torch.fft.rfft(x)[: int(n)].to(torch.complex64)).reshape(-1).contiguous())
-        del x, u
-    return specs
-
-
 def run_batch(args):
     """One persistent CUDA-graph launch over a batch of uneven spectra per step (Gaussian-noise
     time series with 0-4 injected chirps each, synthesised on the device from a seeded generator)."""
@@ -266,10 +235,10 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     fdas_build.build()
-    n_bins, zmax = batch_workload(args.batch_count)
+    n_bins, zmax = synth.batch_workload(args.batch_count)
     zstep, m = 2, 512
     n_z = 2 * (zmax // zstep) + 1
-    specs = batch_spectra(torch, n_bins, zmax, m, dev)
+    specs, _ = synth.batch_spectra(torch, n_bins, zmax, m, dev)
     planes = [torch.empty((int(z), int(n)), dtype=torch.float32, device=dev) for z, n in zip(n_z, n_bins)]
     stream = torch.cuda.current_stream(dev)
     candidates = [1024, 2048, 4096]
@@ -392,15 +361,8 @@ def run_zband(args):
         rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
         point = {"threshold": thr, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
                  "segment_fraction": ps.segment_fraction, "units": int(n_units)}
-        wall = []   # the whole synchronised path at this threshold (L2 flushed before each run)
-        for _ in range(10):
-            flush.fill_(1.0)
-            torch.cuda.synchronize(dev)
-            t1 = time.perf_counter()
-            ps.search(spec, part, thr)
-            torch.cuda.synchronize(dev)
-            wall.append((time.perf_counter() - t1) * 1e3)
-        point["ms"] = statistics.median(wall)
+        # the device-resident path at this threshold, CUDA events (L2 flushed before each run)
+        point["ms"] = event_ms(lambda: ps.search_async(spec, part, thr, stream), 10)
         points.append(point)
     # the same thresholds without segment masks (every segment of a listed unit's group computed)
     ps_group = zb.ProposalSearch(net, plan, segment_masks=False)
@@ -410,16 +372,9 @@ def run_zband(args):
         n_units = ps_group.search(spec, part, thr)
         plan.check()
         rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
-        wall = []
-        for _ in range(10):
-            flush.fill_(1.0)
-            torch.cuda.synchronize(dev)
-            t1 = time.perf_counter()
-            ps_group.search(spec, part, thr)
-            torch.cuda.synchronize(dev)
-            wall.append((time.perf_counter() - t1) * 1e3)
         group_points.append({"threshold": thr, "recall": rec, "unit_fraction": ps_group.unit_fraction,
-                             "units": int(n_units), "ms": statistics.median(wall)})
+                             "units": int(n_units),
+                             "ms": event_ms(lambda: ps_group.search_async(spec, part, thr, stream), 10)})
     del ps_group
     # a denser check of recall: 2^22 bins with a chirp in every 16th block (SNR as in training)
     rng = np.random.default_rng(171110859)
@@ -442,17 +397,23 @@ def run_zband(args):
     for _ in range(args.warmup):
         ps.search(spec, part, thr)
     plan.check()
-    step_ms = []
+    # timed step: the whole path on the device (proposal, work list, correlation with the list
+    # length read on the device), CUDA events on the launching stream; the list length is read
+    # back after the timed region
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        ps.search_async(spec, part, thr, stream)
     torch.cuda.synchronize(dev)
     with ClockSampler(0) as clk:
         time.sleep(0.3)   # a few clock samples before the short timed region
-        for _ in range(args.steps):
+        for e0, e1 in evs:
             flush.fill_(1.0)
-            torch.cuda.synchronize(dev)
-            t1 = time.perf_counter()
-            ps.search(spec, part, thr)
-            torch.cuda.synchronize(dev)
-            step_ms.append((time.perf_counter() - t1) * 1e3)
+            e0.record(stream)
+            ps.search_async(spec, part, thr, stream)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    timed_units = ps.device_units()
     plan.check()
     net.check()
     ms = sum(step_ms) / len(step_ms)
@@ -470,7 +431,8 @@ def run_zband(args):
                    "train_snr": list(args.zband_snr), "train_snr_dist": args.zband_snr_dist,
                    "train_steps": args.zband_steps, "train_s": train_s, "final_loss": losses[-1][1],
                    "l2": "512 MiB buffer written between timed steps",
-                   "timing": "host wall clock around the synchronised path (it reads the list length)"},
+                   "timing": "CUDA events around the device-resident path (list length read on the device, "
+                             "read back after the timed region)", "timed_units": timed_units},
         "recall": points[0]["recall"], "unit_fraction": points[0]["unit_fraction"],
         "full_search_ms": full_ms, "full_search_cells_per_s": cells / (full_ms * 1e-3),
         "propose_ms": propose_ms, "operating_points": points, "operating_points_without_segment_masks": group_points,
@@ -641,10 +603,15 @@ def run_ours(args):
         "template_build_ms": template_build_ms,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
+    del h_plane
     if tc:
         tc_roofline(torch, plan, w, d_spec, stream, ms, line, peaks, peak_src)
         line["accuracy"] = accuracy
-    del h_plane, plane, flush
+    elif w.seg_len == 2048 and not args.no_variants:
+        torch.cuda.empty_cache()
+        line["variants"] = tc_variants(torch, plan, w, d_spec, plane, flush, stream, alg["flops"], peaks, peak_src,
+                                       alu_peak)
+    del plane, flush
     torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
         cores = cpu_cores()
@@ -681,6 +648,53 @@ def tc_accuracy(torch, plan, w, d_spec, plane, stream) -> dict:
     return {"vs": "FP32 path plane (itself within 1e-5 per row of the FP64 oracle in the tests)",
             "max_row_rel_err": float(err.max()), "median_row_rel_err": float(np.median(err)),
             "rows": int(err.size), "chirps_recovered": found, "chirps": len(w.chirps)}
+
+
+def tc_variants(torch, plan, w, d_spec, plane, flush, stream, method_flops: int, peaks, peak_src, alu_peak):
+    """The tensor-core variants of the segment transforms on the same plan and spectrum, beside the
+    FP32 line: per precision, the time per plane (CUDA events over 5 launches after 2 warm-ups,
+    L2 flushed between), the per-row error against the FP32 plane just computed (`plane`), chirp
+    recovery, and two rates: the method's nominal FFT flops (the FP32 line's count) per second,
+    and the dense hi + lo DFT-matrix products the kernel executes against the tensor peak."""
+    out = {"vs": "FP32 path plane of this run (itself within 1e-5 per row of the FP64 oracle in the tests)"}
+    other = torch.empty_like(plane)
+    zs = np.arange(-w.zmax, w.zmax + 1, w.zstep)
+    for prec in ("bf16", "fp16"):
+        for _ in range(2):
+            plan.convolve_power_tc(d_spec, other, prec, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            plan.convolve_power_tc(d_spec, other, prec, stream)
+            e1.record(stream)
+        torch.cuda.synchronize(d_spec.device)
+        plan.check(stream)
+        t = [a.elapsed_time(b) for a, b in evs]
+        ms = statistics.median(t)
+        err = ((other - plane).abs().amax(dim=1) / plane.amax(dim=1)).cpu().numpy()
+        found = 0
+        for c in w.chirps:
+            r0 = int(round(c.r_mean))
+            lo, hi = max(r0 - 64, 0), min(r0 + 65, w.n_bins)
+            win = other[:, lo:hi].cpu().numpy()
+            zi, dr = np.unravel_index(np.argmax(win), win.shape)
+            found += int(abs(zs[zi] - c.z) <= w.zstep + 1e-9 and abs(lo + dr - c.r_mean) <= 1.0)
+        dense = tc_flops(plan.n_seg, plan.n_z)
+        tpk = float(peaks["bf16_tflops"])
+        out[prec] = {"ms_per_plane": ms, "cells_per_s": plan.n_z * w.n_bins / (ms * 1e-3),
+                     "max_row_rel_err": float(err.max()), "median_row_rel_err": float(np.median(err)),
+                     "chirps_recovered": found, "chirps": len(w.chirps),
+                     "method_flops_rate": {"achieved": method_flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                           "flops_per_plane": method_flops,
+                                           "frac_of_fp32_peak": method_flops / (ms * 1e-3) / 1e12 / alu_peak},
+                     "dense_products_rate": {"achieved": dense / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                             "flops_per_plane": dense, "peak": tpk,
+                                             "frac": dense / (ms * 1e-3) / 1e12 / tpk,
+                                             "peak_source": f"bf16_tflops burst ({peak_src})"},
+                     "gpu_launches": 2 * (2 + len(evs))}
+    del other
+    return out
 
 
 def tc_flops(nseg: int, Z: int) -> int:
@@ -780,6 +794,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core variants object")
     ap.add_argument("--n-bins", type=int, default=None, help="profiling only: shorter spectrum, same geometry")
     ap.add_argument("--seg-len", type=int, default=None, help="segment length sweep (default: the workload's)")
     ap.add_argument("--precision", choices=["f32", "bf16", "fp16"], default="f32",

@@ -124,8 +124,9 @@ int fdas_convolve_power(fdas_plan* plan, const float* d_spectrum, float* d_plane
  * seg_len != 2048 or another precision).  The first call on a plan (and the first after
  * fdas_templates_build) allocates and fills a workspace of Z*L*8 + nseg*L*8 + 320 KB bytes; later
  * calls allocate nothing.  Two kernel launches on `stream` (forward transforms into the
- * workspace, then the correlation).  Per-row error against the FP64 definition is a few 1e-6 of
- * the row peak (bound stated by the tests: 2e-4).
+ * workspace, then the correlation).  Per-row error (max over the row of |P_tc - P|, over the
+ * row's peak) on the 2^22-bin, 201-template survey plane: up to 1.1-1.3e-5 with BF16 operands and
+ * about 4e-6 with FP16 (bound stated by the tests: 2e-4).
  */
 #define FDAS_TC_BF16 0
 #define FDAS_TC_FP16 1
@@ -261,6 +262,16 @@ int fdas_convolve_power_units(fdas_plan* plan, const float* d_spectrum, float* d
 int fdas_convolve_power_units_masked(fdas_plan* plan, const float* d_spectrum, float* d_plane,
                                      const int32_t* d_units, const uint16_t* d_masks, int64_t n_units,
                                      fdas_stream_t stream);
+/* As fdas_convolve_power_units_masked (d_masks may be NULL), with the list length read on the
+ * device from *d_count (int64, 8-byte aligned: e.g. the length fdas_zband_work_units_masked
+ * leaves in its workspace) instead of passed by the host, so that a proposal, its work list and
+ * the correlation run without a host synchronisation.  max_units >= 1 is the capacity of d_units
+ * (and d_masks); a *d_count outside [0, max_units] fails the device-side check like a bad list
+ * (nothing runs, the next fdas_check() returns FDAS_ERR_INVALID).  The paper has no
+ * counterpart. */
+int fdas_convolve_power_units_device_count(fdas_plan* plan, const float* d_spectrum, float* d_plane,
+                                           const int32_t* d_units, const uint16_t* d_masks, const int64_t* d_count,
+                                           int64_t max_units, fdas_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Learned z-band proposal (no counterpart in the paper): a 1-D convolutional network over the
@@ -337,7 +348,10 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
  * its length to *host_count (synchronises `stream`).  d_scratch: device workspace of at least
  * fdas_zband_work_units_scratch_bytes(n_groups, Z) bytes, 16-byte aligned, caller-owned, or
  * NULL for stream-ordered allocations inside the call (which the memory pool may return to the
- * system at the synchronisation, making every call map them again). */
+ * system at the synchronisation, making every call map them again).  With a caller workspace,
+ * host_count may be NULL: the call is then fully asynchronous and the length stays on the device,
+ * as the int64 at ((const int64_t*)d_scratch)[n_groups], for
+ * fdas_convolve_power_units_device_count. */
 int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z);
 int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
                           int64_t group_bins, int h, int64_t n_groups, int32_t* d_units, void* d_scratch,

@@ -203,3 +203,172 @@ def work_unit_masks(logits: np.ndarray, threshold: float, hop: int, seg_bins: in
                 units.append(g * Z + z)
                 masks.append(m)
     return np.asarray(units, dtype=np.int64), np.asarray(masks, dtype=np.int64)
+
+
+# ---------------------------------------------------------------------------------------------
+# Rounding-error bounds of the finite-precision kernels (the tolerances of the GPU tests)
+#
+# Model (Higham & Mary, "A new approach to probabilistic rounding error analysis", SIAM J. Sci.
+# Comput. 41 (2019)): every rounding -- the FP16 storage of an input or activation value v, each
+# addition of a floating-point sum -- contributes an independent, mean-zero error bounded by
+# u |v| (by u |partial sum| for an addition).  To first order a kernel output y then differs from
+# its FP64 value by sum_r J_r delta_r over the roundings r, J_r the exact derivative of y with
+# respect to r, and Hoeffding's inequality gives |delta y| <= lam * sqrt(sum_r (J_r e_r)^2) with
+# probability at least 1 - 2 exp(-lam^2 / 2) (lam = 10: 4e-22).  A sum of n terms is represented
+# by one error of scale sqrt(n) u S (S the sum of the term magnitudes), which bounds
+# sqrt(sum_k partial_k^2) u.  Worst-case bounds (all errors aligned) are vacuous here: the FP16
+# network's logits would be allowed to move by more than half their scale.
+# ---------------------------------------------------------------------------------------------
+
+U16 = 2.0 ** -11          # FP16 round-to-nearest unit roundoff
+U32 = 2.0 ** -24          # FP32 round-to-nearest unit roundoff
+LAMBDA = 10.0             # confidence multiplier of the probabilistic bounds
+
+
+def _conv_t(w: np.ndarray, dout: np.ndarray, d: int) -> np.ndarray:
+    """Input gradient of conv_k9 (the transposed convolution), with BLAS matrix products."""
+    B, O, T = dout.shape
+    P = PAD * d
+    dxp = np.zeros((B, w.shape[1], T + 2 * P))
+    for k in range(K):
+        dxp[:, :, k * d:k * d + T] += np.matmul(w[:, :, k].T, dout)
+    return dxp[:, :, P:P + T]
+
+
+def _conv_abs(x: np.ndarray, w: np.ndarray, b: np.ndarray | None, d: int) -> np.ndarray:
+    """Sums of term magnitudes of a layer: conv_k9 with |w| and |b| on a non-negative array."""
+    B, I, T = x.shape
+    P = PAD * d
+    xp = np.zeros((B, I, T + 2 * P))
+    xp[:, :, P:P + T] = x
+    out = np.zeros((B, w.shape[0], T))
+    aw = np.abs(w)
+    for k in range(K):
+        out += np.matmul(aw[:, :, k], xp[:, :, k * d:k * d + T])
+    return out if b is None else out + np.abs(b)[None, :, None]
+
+
+def logits_error_bound(params: dict, x: np.ndarray, x_u: float, act_u: float, acc_u: float, head_u: float,
+                       layer_terms=(17, 289, 289), head_terms: int = 33, lam: float = LAMBDA):
+    """Logits (FP64) and, per logit, the probabilistic bound lam * sqrt(sum_r (J_r e_r)^2) on the
+    distance of a kernel that: holds the input with relative rounding x_u; accumulates layer l's
+    pre-activation (bias included) as a sum of layer_terms[l] terms with unit roundoff acc_u; stores
+    the relu outputs of layers 1 and 2 with relative rounding act_u; max-pools layer 3 exactly; sums
+    the head (bias and 32 products) with unit roundoff head_u.  params are the values the kernel
+    uses.  J is evaluated exactly for every logit by a backward pass through the network."""
+    logits, c = forward(params, x, keep=True)
+    B = logits.shape[0]
+    Z = params["Wl"].shape[0]
+    e_x = x_u * np.abs(c["h0"])
+    e_h = {1: act_u * c["h1"], 2: act_u * c["h2"]}
+    e_acc = {}
+    h_prev = c["h0"]
+    for layer in range(3):
+        S = _conv_abs(np.abs(h_prev), params[f"W{layer + 1}"], params[f"b{layer + 1}"], DIL[layer])
+        e_acc[layer + 1] = np.sqrt(layer_terms[layer]) * acc_u * S
+        h_prev = c[f"h{layer + 1}"]
+    Wl, bl = params["Wl"], params["bl"]
+    var = np.zeros((B, Z))
+    var += (np.sqrt(head_terms) * head_u * (np.abs(bl)[None, :] + c["m"] @ np.abs(Wl).T)) ** 2
+    bi, ci = np.arange(B)[:, None], np.arange(c["a3"].shape[1])[None, :]
+    mask3 = np.take_along_axis(c["a3"], c["arg"][:, :, None], axis=2)[:, :, 0] > 0
+    for j in range(Z):
+        da3 = np.zeros_like(c["a3"])
+        da3[bi, ci, c["arg"]] = Wl[j][None, :] * mask3
+        var[:, j] += np.sum((da3 * e_acc[3]) ** 2, axis=(1, 2))
+        dh2 = _conv_t(params["W3"], da3, DIL[2])
+        var[:, j] += np.sum((dh2 * e_h[2]) ** 2, axis=(1, 2))
+        da2 = dh2 * (c["a2"] > 0)
+        var[:, j] += np.sum((da2 * e_acc[2]) ** 2, axis=(1, 2))
+        dh1 = _conv_t(params["W2"], da2, DIL[1])
+        var[:, j] += np.sum((dh1 * e_h[1]) ** 2, axis=(1, 2))
+        da1 = dh1 * (c["a1"] > 0)
+        var[:, j] += np.sum((da1 * e_acc[1]) ** 2, axis=(1, 2))
+        dh0 = _conv_t(params["W1"], da1, DIL[0])
+        var[:, j] += np.sum((dh0 * e_x) ** 2, axis=(1, 2))
+    return logits, lam * np.sqrt(var)
+
+
+def grads_error_bound(params: dict, x: np.ndarray, target: np.ndarray, tile: int = 128, lam: float = LAMBDA):
+    """Gradients (FP64) and per-entry bounds lam * sigma for the FP32 training kernels, sigma
+    propagated layer by layer (each value's error treated as independent of its neighbours'):
+    forward sums by FMA chains (bias first, then CIN*9 products), FP32 activations, exact
+    pooling, head by an FMA chain over 32 channels; dlog = (sigmoid(l) - t)/N with the sigmoid
+    within 8 ulp at the computed logit; head gradients over the batch (two roundings per term);
+    data gradients by FMA chains over (o, k) or over j; weight gradients as tile-long FMA chains
+    per (window, tile) block summed over the blocks.  Where a relu mask or the pooled position is
+    within lam * sigma of changing, the gradient may take either branch: the bound then adds the
+    full magnitude of that branch's term."""
+    x = np.asarray(x, dtype=np.float64)
+    B, T = x.shape
+    Z = params["Wl"].shape[0]
+    logits, c = forward(params, x, keep=True)
+    _, g = loss_and_grads(params, x, target)
+    # forward sigmas (FP32 path: x exact, no storage rounding beyond each sum's own)
+    sig_a = {}
+    var_h = np.zeros_like(c["h0"])
+    h_prev = c["h0"]
+    for layer in range(3):
+        W, b, d = params[f"W{layer + 1}"], params[f"b{layer + 1}"], DIL[layer]
+        n = (1 if layer == 0 else 32) * K + 1
+        S = _conv_abs(np.abs(h_prev), W, b, d)
+        v = _conv_abs(var_h, W ** 2, None, d) + n * (U32 * S) ** 2
+        sig_a[layer + 1] = np.sqrt(v)
+        var_h = v
+        h_prev = c[f"h{layer + 1}"]
+    lo, hi = T // 4, 3 * T // 4
+    bi, ci = np.arange(B)[:, None], np.arange(c["a3"].shape[1])[None, :]
+    m, arg = c["m"], c["arg"]
+    sig_m = sig_a[3][bi, ci, arg]
+    Wl, bl = params["Wl"], params["bl"]
+    sig_l = np.sqrt((sig_m ** 2) @ (Wl ** 2).T + 33 * (U32 * (np.abs(bl)[None, :] + m @ np.abs(Wl).T)) ** 2)
+    n_log = logits.size
+    s = 1.0 / (1.0 + np.exp(-logits))
+    dlog = (s - target) / n_log
+    sig_dlog = (0.25 * sig_l + 8 * U32 * s + 2 * U32 * np.abs(s - target)) / n_log
+    bnd = {}
+    bnd["Wl"] = np.sqrt((sig_dlog ** 2).T @ (m ** 2) + (dlog ** 2).T @ (sig_m ** 2)
+                        + 2 * B * (U32 * (np.abs(dlog).T @ m)) ** 2)
+    bnd["bl"] = np.sqrt((sig_dlog ** 2).sum(axis=0) + B * (U32 * np.abs(dlog).sum(axis=0)) ** 2)
+    dm = dlog @ Wl
+    sig_dm = np.sqrt((sig_dlog ** 2) @ (Wl ** 2) + Z * (U32 * (np.abs(dlog) @ np.abs(Wl))) ** 2)
+    # pooled gradient; positions that could take the maximum, or whose relu could flip, take it all
+    a3, h3 = c["a3"], c["h3"]
+    da3 = np.zeros_like(a3)
+    da3[bi, ci, arg] = dm * (a3[bi, ci, arg] > 0)
+    sd3 = np.zeros_like(a3)
+    sd3[bi, ci, arg] = sig_dm
+    # a central position can carry the pooled gradient if, perturbed, it can reach the maximum
+    # and be positive; the gradient is decided when only the pooled position can
+    hi_a = a3 + lam * sig_a[3]
+    cand = np.zeros_like(a3, dtype=bool)
+    cand[:, :, lo:hi] = (hi_a[:, :, lo:hi] >= (m - lam * sig_m)[:, :, None]) & (hi_a[:, :, lo:hi] > 0)
+    pooled_pos = np.zeros_like(cand)
+    pooled_pos[bi, ci, arg] = a3[bi, ci, arg] - lam * sig_m > 0      # surely positive at the maximum
+    decided = (cand.sum(axis=2) == pooled_pos.sum(axis=2)) & ((cand & ~pooled_pos).sum(axis=2) == 0)
+    extra = np.where((~decided)[:, :, None] & cand, (np.abs(dm) + lam * sig_dm)[:, :, None], 0.0)
+    nblk = B * (T // tile)
+    w_terms = tile + nblk
+    delta, sig_d, extra_d = da3, sd3, extra
+    for layer in (3, 2, 1):
+        W, d = params[f"W{layer}"], DIL[layer - 1]
+        h_in = c[f"h{layer - 1}"]
+        sig_h = np.zeros_like(h_in) if layer == 1 else sig_a[layer - 1]
+        _, v1, _ = conv_k9_backward(sig_h ** 2, W, delta ** 2, d)
+        _, v2, _ = conv_k9_backward(h_in ** 2, W, sig_d ** 2, d)
+        _, mag, _ = conv_k9_backward(np.abs(h_in), W, np.abs(delta), d)
+        _, ext, _ = conv_k9_backward(np.abs(h_in), W, extra_d, d)
+        bnd[f"W{layer}"] = lam * np.sqrt(v1 + v2 + w_terms * (U32 * mag) ** 2) + ext
+        bnd[f"b{layer}"] = (lam * np.sqrt((sig_d ** 2).sum(axis=(0, 2)) + w_terms * (U32 * np.abs(delta).sum(axis=(0, 2))) ** 2)
+                            + extra_d.sum(axis=(0, 2)))
+        if layer == 1:
+            break
+        a_prev, sa_prev = c[f"a{layer - 1}"], sig_a[layer - 1]
+        dh = _conv_t(W, delta, d)
+        v = _conv_t(W ** 2, sig_d ** 2, d) + (32 * K) * (U32 * _conv_t(np.abs(W), np.abs(delta), d)) ** 2
+        ext_h = _conv_t(np.abs(W), extra_d, d)
+        flip = np.abs(a_prev) <= lam * sa_prev
+        delta = dh * (a_prev > 0)
+        sig_d = np.sqrt(v) * (a_prev > 0)
+        extra_d = np.where(flip, np.abs(dh) + lam * np.sqrt(v), 0.0) + ext_h * ((a_prev > 0) | flip)
+    return g, bnd

@@ -441,6 +441,32 @@ int fdas_convolve_power_units_masked(fdas_plan* p, const float* d_spectrum, floa
   return enqueued(p, st, fdas::launch_units(p->L, q, d_units, d_masks, n_units, p->sm_count, st));
 }
 
+int fdas_convolve_power_units_device_count(fdas_plan* p, const float* d_spectrum, float* d_plane,
+                                           const int32_t* d_units, const uint16_t* d_masks, const int64_t* d_count,
+                                           int64_t max_units, fdas_stream_t stream) {
+  if (!p || !d_spectrum || !d_plane || !d_units || !d_count || max_units < 1) return FDAS_ERR_INVALID;
+  if (!p->built) return FDAS_ERR_NOT_BUILT;
+  if (fdas::batch_segments_per_cta(p->L) == 0) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u) ||
+      (reinterpret_cast<uintptr_t>(d_units) & 3u) || (reinterpret_cast<uintptr_t>(d_masks) & 1u) ||
+      (reinterpret_cast<uintptr_t>(d_count) & 7u))
+    return FDAS_ERR_ALIGN;
+  fdas::ConvParams q;
+  q.spectrum = reinterpret_cast<const float2*>(d_spectrum);
+  q.templates = p->d_templates;
+  q.twist = p->d_twist;
+  q.plane = d_plane;
+  q.status = p->d_status;
+  q.n_bins = p->n_bins;
+  q.nseg = p->nseg;
+  q.units = 0;
+  q.Z = p->Z;
+  q.V = p->V;
+  q.h = p->h;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_units(p->L, q, d_units, d_masks, max_units, p->sm_count, st, d_count));
+}
+
 int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_units,
                               int64_t n_units, fdas_stream_t stream) {
   return fdas_convolve_power_units_masked(p, d_spectrum, d_plane, d_units, nullptr, n_units, stream);

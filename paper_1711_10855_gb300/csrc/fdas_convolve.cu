@@ -30,9 +30,13 @@
 // so every CTA does the same number of inverse transforms.  P warps share a segment and take
 // alternate templates.
 #include <cstdio>
+#include <type_traits>
 
 #include "fdas_device.cuh"
 #include "fdas_internal.h"
+
+// The decoupled work-list instantiation leaves the shared-ring loop of the kernel unreachable.
+#pragma nv_diag_suppress 128
 
 namespace fdas {
 
@@ -100,8 +104,13 @@ __device__ __forceinline__ void apply_twist2(cp2 (&v)[Cfg::H2], const float4* __
 // and runs two N1-point DFTs in lockstep.  Round r moves rows j in [r*N1, (r+1)*N1) through a
 // tile of N1 rows x XCOLS lanes (XR sub-rounds, lanes [h*XCOLS, (h+1)*XCOLS) writing in turn).
 // out(r, n1, pair) receives (y[t + N1*r + N2*n1], y[t + N1*(r+CP) + N2*n1]).
-template <class Cfg, int SIGN, class Out>
-__device__ __forceinline__ void exchange_and_pass2(cp2 (&v)[Cfg::H2], float4* xb, int k1, Out&& out) {
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <class Cfg, int SIGN, class Out, class AfterReads = NoHook>
+__device__ __forceinline__ void exchange_and_pass2(cp2 (&v)[Cfg::H2], float4* xb, int k1, Out&& out,
+                                                   AfterReads&& after_reads = AfterReads{}) {
   static_for<Cfg::CP>([&](auto rr) {
     constexpr int r = decltype(rr)::value;
     cp2 u[Cfg::N1];
@@ -122,6 +131,7 @@ __device__ __forceinline__ void exchange_and_pass2(cp2 (&v)[Cfg::H2], float4* xb
         u[bitrev(src, Cfg::LOG_N1)] = cp2_from(xb[k1 * Cfg::XPITCH + c]);
       });
     });
+    if constexpr (r == Cfg::CP - 1) after_reads();   // the tile is free once its last round is read
     fft_pair_columns<Cfg::N1, SIGN>(u);
     static_for<Cfg::N1>([&](auto nn) {
       constexpr int n1 = decltype(nn)::value;
@@ -424,6 +434,11 @@ __device__ __forceinline__ SpecDesc spectrum_desc(const BatchParams& p, int b) {
   return p.descs == nullptr ? p.single : p.descs[b];
 }
 
+// Units to compute: all of them, or the list length (from device memory when the list was made on
+// the device; the check kernel has bounded it by the list's capacity p.units).
+__device__ __forceinline__ int64_t unit_total(const BatchParams& p) { return p.units; }
+__device__ __forceinline__ int64_t unit_total(const ListParams& p) { return p.unit_count ? *p.unit_count : p.units; }
+
 // NV: pass-2 output rows n1 < NV can hold valid outputs (NV >= ceil(V / N2)); rows n1 >= NV are
 // dropped at compile time, which also removes the butterfly halves that only feed them.
 //
@@ -431,8 +446,17 @@ __device__ __forceinline__ SpecDesc spectrum_desc(const BatchParams& p, int b) {
 // takes a contiguous equal range.  Segment s of spectrum b is brought in by one bulk copy of its
 // part inside [0, n_b) (cp.async.bulk) and the rest of the L-bin window is zero-filled by the
 // owning warp.
-template <class Cfg, int NV, bool LIST>
-__global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchParams p) {
+//
+// DEC (work lists with segment masks only): the warps are decoupled.  Instead of the shared
+// template ring, each warp walks only the positions where one of its segments is listed and
+// brings that position's template into its own shared region by a bulk copy, issued as soon as
+// the region's exchange tile has been read (so it lands while the warp finishes the previous
+// transform).  The time of a group is then set by its busiest warp, not by the number of listed
+// units: sparse masks cost about their share of (segment, template) pairs.
+template <class Cfg, int NV, bool LIST, bool DEC = false>
+__global__ void __launch_bounds__(256, 1)
+    fdas_convolve_tmem_kernel(const std::conditional_t<LIST, ListParams, BatchParams> p) {
+  static_assert(!DEC || LIST, "decoupled warps serve masked work lists");
   constexpr int L = Cfg::L, N1 = Cfg::N1, R = Cfg::R, G = Cfg::G, H2 = Cfg::H2, W = Cfg::W;
   extern __shared__ __align__(1024) unsigned char smem[];
   float2* sT = reinterpret_cast<float2*>(smem + Cfg::OFF_T);
@@ -450,6 +474,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     int b, z, Z, z_off; // its spectrum, template index within it, that spectrum's Z and bank offset
   };
   IssueCursor* cur = reinterpret_cast<IssueCursor*>(smem + Cfg::OFF_BAR + 128);
+  uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + Cfg::OFF_BAR + 192);   // [W] per-warp template copies (DEC)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gw = lane / N1, k1 = lane % N1;
@@ -457,7 +482,12 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   float2* mySeg = myRegion + (size_t)gw * L;
   float4* myXb = reinterpret_cast<float4*>(myRegion) + gw * Cfg::XGROUP;
 
-  const int64_t U = p.units;
+  // a work list that failed its check (kStatusBadList, set by the preceding check kernel) is not
+  // run
+  if constexpr (LIST) {
+    if (*reinterpret_cast<volatile const int*>(p.status) & kStatusBadList) return;
+  }
+  const int64_t U = unit_total(p);
   // flattened unit of list entry e (identity without a work list)
   auto unit_at = [&](int64_t e) -> int64_t {
     if constexpr (LIST) return (int64_t)__ldg(p.unit_list + e);
@@ -467,10 +497,6 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   const int64_t u1 = ((int64_t)blockIdx.x + 1) * U / gridDim.x;
   const int64_t npos = u1 - u0;
   if (npos <= 0) return;
-  // a work list that failed its check (kStatusBadList, set by the preceding check kernel) is not run
-  if constexpr (LIST) {
-    if (*reinterpret_cast<volatile const int*>(p.status) & kStatusBadList) return;
-  }
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) {
@@ -479,6 +505,8 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
       issued_pos[r] = -1;
     }
     mbar_init(segbar, 1);
+    if constexpr (DEC)
+      for (int w = 0; w < W; ++w) mbar_init(&wbar[w], 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -517,7 +545,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
       cur->spec_end = nb + 1 < p.count ? spectrum_desc(p, nb + 1).unit_base : U;
     }
   };
-  if (tid == 0) {
+  if (tid == 0 && !DEC) {
     const int b0 = find_spectrum(p, u0);
     const SpecDesc d0 = spectrum_desc(p, b0);
     cur->u = u0;
@@ -565,6 +593,8 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
   int alive = 1;
   uint32_t seg_phase = 0;
   bool seg_in_flight = false;
+  uint32_t w_phase = 0;        // DEC: parity of this warp's next template copy
+  bool w_in_flight = false;    // DEC: a copy into this warp's region not yet waited for
   int64_t u = u0;
   while (u < u1) {
     // the segment group holding entry u (a run of list entries with the same group)
@@ -642,6 +672,85 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     const int64_t segbase = s * (int64_t)p.V;
     const int64_t lim64 = d.n_bins - segbase < (int64_t)p.V ? d.n_bins - segbase : (int64_t)p.V;
     const int lim = lim64 > 0 ? (int)lim64 : 0;
+    if constexpr (DEC) {
+      // this warp's segment bits of list position i (warp-uniform)
+      auto warp_bits = [&](int64_t i) -> unsigned {
+        return ((unsigned)__ldg(p.unit_mask + u0 + i) >> (warp * Cfg::F)) & ((1u << Cfg::F) - 1u);
+      };
+      auto next_active = [&](int64_t i) {
+        while (i < bpos && warp_bits(i) == 0u) ++i;
+        return i;
+      };
+      // template of position i into this warp's region (lane 0; the region's earlier generic
+      // accesses are ordered before the asynchronous copy)
+      auto fetch = [&](int64_t i) {
+        __syncwarp();
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          const int64_t zrow = unit_at(u0 + i) % d.Z;
+          mbar_arrive_expect_tx(&wbar[warp], L * 8);
+          bulk_g2s(myRegion, p.templates + (size_t)zrow * L, L * 8, &wbar[warp]);
+        }
+        w_in_flight = true;
+      };
+      int64_t i = next_active(a);
+      if (i < bpos) fetch(i);
+      while (i < bpos) {
+        const int ok = __all_sync(0xffffffffu, wait_slot(&wbar[warp], w_phase, abort_flag));
+        w_in_flight = false;
+        w_phase ^= 1u;
+        if (!ok) {
+          if (lane == 0) report_timeout(p.status, abort_flag);
+          break;
+        }
+        const int64_t z = unit_at(u0 + i) % d.Z;
+        const int lim_z = ((warp_bits(i) >> gw) & 1u) ? lim : 0;
+        const float4* st4 = reinterpret_cast<const float4*>(myRegion);
+        cp2 v[H2];
+        static_for<H2 / 8>([&](auto cc) {
+          constexpr int c = decltype(cc)::value;
+          float x0[16], x1[16];
+          tmem_ld16(x_addr + 32 * c, x0);
+          tmem_ld16(x_addr + 32 * c + 16, x1);
+          float4 t[8];
+          static_for<8>([&](auto qq) {
+            constexpr int q = decltype(qq)::value;
+            t[q] = st4[(8 * c + q) * N1 + k1];
+          });
+          tmem_wait_ld();
+          static_for<8>([&](auto qq) {
+            constexpr int q = decltype(qq)::value;
+            constexpr int pp = 8 * c + q;
+            const float* xs = q < 4 ? &x0[4 * q] : &x1[4 * (q - 4)];
+            const cp2 x = cp2{make_float2(xs[0], xs[1]), make_float2(xs[2], xs[3])};
+            v[bitrev(2 * pp, Cfg::LOG_N2)] = cmul2(x, cp2_from(t[q]));
+          });
+        });
+        const int64_t inext = next_active(i + 1);
+        fft_split_pairs<Cfg::N2, +1>(v);
+        apply_twist_tmem<Cfg, false>(v, tw_addr);
+        float* row = d.plane + z * d.n_bins + segbase;
+        exchange_and_pass2<Cfg, +1>(
+            v, myXb, k1,
+            [&](auto, auto nn, const cp2& y) {
+              constexpr int n1 = decltype(nn)::value;
+              if constexpr (n1 < NV) {
+                const float2 pw = power2(y);
+                const int n_lo = k1 + Cfg::N2 * n1;
+                const int n_hi = n_lo + N1;
+                if (n_lo < lim_z) __stcs(row + n_lo, pw.x);
+                if (n_hi < lim_z) __stcs(row + n_hi, pw.y);
+              }
+            },
+            [&]() {
+              if (inext < bpos) fetch(inext);
+            });
+        i = inext;
+      }
+      // after a timeout the abort flag is set: every warp leaves at the group barrier above
+      tmem_fence_before_sync();
+      continue;
+    }
     for (int64_t i = a; i < bpos; ++i) {
       const int slot = (int)(i % R);
       const int ok = __all_sync(0xffffffffu, wait_slot(&full[slot], (uint32_t)((i / R) & 1), abort_flag));
@@ -720,6 +829,9 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_tmem_kernel(const BatchP
     for (int r = 0; r < R; ++r)
       if (issued_pos[r] >= 0) (void)mbar_wait(&full[r], (uint32_t)((issued_pos[r] / R) & 1));
     if (seg_in_flight) (void)mbar_wait(segbar, seg_phase);
+  }
+  if constexpr (DEC) {
+    if (lane == 0 && w_in_flight) (void)mbar_wait(&wbar[warp], w_phase);   // bounded
   }
   if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
 }
@@ -811,19 +923,32 @@ using Cfg1024 = ConvCfg<1024, 16, 2, 1>;
 using Cfg2048 = ConvCfg<2048, 32, 4, 1, 2>;
 
 template <class Cfg, int NV>
-static cudaError_t launch_tmem_nv(const BatchParams& p, int sm_count, cudaStream_t st) {
-  // the work-list variant is a separate instantiation: the full-plane code stays free of it
-  auto kern = p.unit_list ? fdas_convolve_tmem_kernel<Cfg, NV, true> : fdas_convolve_tmem_kernel<Cfg, NV, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-  if (e != cudaSuccess) return e;
+static cudaError_t launch_tmem_nv(const ListParams& p, int sm_count, cudaStream_t st) {
+  // the work-list variant is a separate instantiation (with its own parameter type): the
+  // full-plane code stays free of it
   const int64_t grid = p.units < sm_count ? p.units : sm_count;
-  kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(p);
+  if (p.unit_list && p.unit_mask) {
+    auto kern = fdas_convolve_tmem_kernel<Cfg, NV, true, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(p);
+  } else if (p.unit_list) {
+    auto kern = fdas_convolve_tmem_kernel<Cfg, NV, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(p);
+  } else {
+    auto kern = fdas_convolve_tmem_kernel<Cfg, NV, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, 256, Cfg::SMEM, st>>>(static_cast<const BatchParams&>(p));
+  }
   return cudaGetLastError();
 }
 
 // Smallest instantiated NV >= ceil(V / N2): N1*3/4, N1*7/8 or N1.
 template <class Cfg>
-static cudaError_t launch_tmem_cfg(const BatchParams& p, int sm_count, cudaStream_t st) {
+static cudaError_t launch_tmem_cfg(const ListParams& p, int sm_count, cudaStream_t st) {
   const int rows = (p.V + Cfg::N2 - 1) / Cfg::N2;
   if (rows <= Cfg::N1 * 3 / 4) return launch_tmem_nv<Cfg, Cfg::N1 * 3 / 4>(p, sm_count, st);
   if (rows <= Cfg::N1 * 7 / 8) return launch_tmem_nv<Cfg, Cfg::N1 * 7 / 8>(p, sm_count, st);
@@ -838,12 +963,18 @@ int batch_segments_per_cta(int L) {
   }
 }
 
-cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t st) {
+static cudaError_t launch_desc(int L, const ListParams& p, int sm_count, cudaStream_t st) {
   switch (L) {
     case 512: return launch_tmem_cfg<TmemCfg<512, 16>>(p, sm_count, st);
     case 2048: return launch_tmem_cfg<TmemCfg<2048, 32>>(p, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t st) {
+  ListParams q;
+  static_cast<BatchParams&>(q) = p;
+  return launch_desc(L, q, sm_count, st);
 }
 
 // Single spectrum: the descriptor-driven kernel with an inline one-entry table where it exists.
@@ -872,7 +1003,17 @@ static cudaError_t launch_single_desc(int L, const ConvParams& p, int sm_count, 
 
 // A work list is usable when its entries are strictly increasing and inside [0, limit): that
 // bounds every template row, segment and plane row the kernel touches.  Otherwise kStatusBadList.
-__global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limit, int* status) {
+// With d_count the length is read from device memory and must lie in [0, n] (n = the list's capacity).
+__global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limit, int* status,
+                                   const int64_t* d_count) {
+  if (d_count) {
+    const int64_t c = *d_count;
+    if (c < 0 || c > n) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusBadList);
+      return;
+    }
+    n = c;
+  }
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = units[e];
     if (u < 0 || u >= limit || (e > 0 && (int64_t)units[e - 1] >= u)) atomicOr(status, kStatusBadList);
@@ -880,16 +1021,16 @@ __global__ void check_units_kernel(const int32_t* units, int64_t n, int64_t limi
 }
 
 cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const uint16_t* masks, int64_t n_units,
-                         int sm_count, cudaStream_t st) {
+                         int sm_count, cudaStream_t st, const int64_t* d_count) {
   const int G = batch_segments_per_cta(L);
   if (G == 0 || n_units < 1) return cudaErrorInvalidValue;
   const int64_t ngroups = (p.nseg + G - 1) / G;
   {
     const int64_t blocks = (n_units + 255) / 256;
     const unsigned grid = (unsigned)(blocks < 4LL * sm_count ? blocks : 4LL * sm_count);
-    check_units_kernel<<<grid, 256, 0, st>>>(units, n_units, ngroups * p.Z, p.status);
+    check_units_kernel<<<grid, 256, 0, st>>>(units, n_units, ngroups * p.Z, p.status, d_count);
   }
-  BatchParams q;
+  ListParams q;
   q.templates = p.templates;
   q.twist = p.twist;
   q.status = p.status;
@@ -906,9 +1047,10 @@ cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const
   q.units = n_units;
   q.unit_list = units;
   q.unit_mask = masks;
+  q.unit_count = d_count;   // with a device count, n_units is the list's capacity (grid: every SM)
   q.V = p.V;
   q.h = p.h;
-  return launch_batch(L, q, sm_count, st);
+  return launch_desc(L, q, sm_count, st);
 }
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {

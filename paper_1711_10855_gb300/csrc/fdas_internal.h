@@ -52,6 +52,13 @@ struct BatchParams {
   const uint16_t* unit_mask = nullptr;
 };
 
+// The work-list instantiation's parameters: a BatchParams plus the list length in device memory
+// (read by the kernel), or nullptr: `units` entries.  A separate type keeps the full-plane kernel's
+// parameters, and so its code, free of the work-list fields.
+struct ListParams : BatchParams {
+  const int64_t* unit_count = nullptr;
+};
+
 // Parameters of the forward-transform-only kernel (steps a2 + a3, for tests).
 struct SegParams {
   const float2* twist;
@@ -76,7 +83,7 @@ int batch_segments_per_cta(int L);
 cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t stream);
 // Single spectrum restricted to a work list of units g*Z + z (ascending).
 cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const uint16_t* masks, int64_t n_units, int sm_count,
-                         cudaStream_t stream);
+                         cudaStream_t stream, const int64_t* d_count = nullptr);
 
 // Launch helpers (defined in fdas_convolve.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_convolve(int L, const CUtensorMap* spec_map, const ConvParams& p, int sm_count,

@@ -217,8 +217,9 @@ __global__ void pool_head_kernel(const float* a3, const WT* Wl, const WT* bl, in
   }
 }
 
-// dlog = (sigmoid(l) - target) / (B*Z); loss accumulated into *loss (sum of BCE terms / (B*Z)).
-__global__ void bce_grad_kernel(const float* logits, const float* target, int count, float* dlog, float* loss) {
+// dlog = (sigmoid(l) - target) / (B*Z); loss_part[warp] = that warp's sum of BCE terms / (B*Z),
+// summed afterwards in a fixed order (sum_fixed_kernel), so the loss is the same on every run.
+__global__ void bce_grad_kernel(const float* logits, const float* target, int count, float* dlog, float* loss_part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float term = 0.f;
   if (i < count) {
@@ -227,7 +228,32 @@ __global__ void bce_grad_kernel(const float* logits, const float* target, int co
     term = fmaxf(l, 0.f) - l * t + log1pf(expf(-fabsf(l)));
   }
   for (int off = 16; off > 0; off >>= 1) term += __shfl_down_sync(0xffffffffu, term, off);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, term / (float)count);
+  if ((threadIdx.x & 31) == 0 && i < count) loss_part[i >> 5] = term / (float)count;   // warps with a term
+}
+
+// out = sum of part[0..n) in a fixed order: thread t adds part[t], part[t + 1024], ... in turn,
+// then a fixed-shape tree over the 1024 threads.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) sum_fixed_kernel(const float* part, int n, float* out) {
+  __shared__ float s[1024];
+  float a = 0.f;
+  for (int j = threadIdx.x; j < n; j += 1024) a += part[j];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// out[j] = sum over blk = 0, 1, ..., nblk-1 (in that order) of part[blk * stride + j], j < n: the
+// fixed-order reduction of per-block weight-gradient partials.
+__global__ void reduce_partials_kernel(const float* part, int nblk, int stride, int n, float* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float a = 0.f;
+  for (int blk = 0; blk < nblk; ++blk) a += part[(size_t)blk * stride + j];
+  out[j] = a;
 }
 
 // Head backward: dWl[j][c] = sum_b dlog[b][j] m[b][c], dbl[j] = sum_b dlog[b][j].
@@ -294,16 +320,18 @@ __global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* dout, c
   }
 }
 
-// dW[o][i][k] += sum_{t in tile} in(b, i, t + (k - 4) D) * dOut[b][o][t]; db[o] += sum dOut.
-// Block (tile, b); thread handles (o = tid/8) and i in {tid%8, tid%8 + 8, ...}.
+// Partials of one block (tile, b): part[blk][(o*CIN + i)*9 + k] = sum_{t in tile} in(b, i, t + (k - 4) D)
+// * dOut[b][o][t] and part[blk][C*CIN*9 + o] = sum_{t in tile} dOut[b][o][t], blk = b*tiles + tile;
+// reduce_partials_kernel then sums them over blocks in a fixed order (no floating-point atomics, so
+// one seed gives one network).  Thread handles (o = tid/8) and i in {tid%8, tid%8 + 8, ...}.
 template <int CIN, int D>
 constexpr size_t bwd_weight_smem() {
   return sizeof(float) * ((size_t)CIN * (kTile + 2 * kPad * D) + (size_t)kC * kTile);
 }
 
 template <int CIN, bool RELU_IN, int D>
-__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, const float* dout, int Wd, float* dW,
-                                                              float* db) {
+__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, const float* dout, int Wd,
+                                                              float* part) {
   constexpr int S = kTile + 2 * kPad * D;
   extern __shared__ float dyn[];
   float (*sIn)[S] = reinterpret_cast<float (*)[S]>(dyn);
@@ -331,13 +359,14 @@ __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* in, c
 #pragma unroll
       for (int k = 0; k < kK; ++k) acc[k] = fmaf(sIn[i][t + k * D], d, acc[k]);
     }
+    float* dst = part + ((size_t)b * gridDim.x + blockIdx.x) * ((size_t)kC * CIN * kK + kC);
 #pragma unroll
-    for (int k = 0; k < kK; ++k) atomicAdd(&dW[(o * CIN + i) * kK + k], acc[k]);
+    for (int k = 0; k < kK; ++k) dst[(o * CIN + i) * kK + k] = acc[k];
   }
   if (l == 0) {
     float s = 0.f;
     for (int t = 0; t < kTile; ++t) s += sD[o][t];
-    atomicAdd(&db[o], s);
+    part[((size_t)b * gridDim.x + blockIdx.x) * ((size_t)kC * CIN * kK + kC) + (size_t)kC * CIN * kK + o] = s;
   }
 }
 
@@ -801,6 +830,8 @@ struct fdas_zband {
   float* logits = nullptr;   // [B][Z]
   float* dlog = nullptr;     // [B][Z]
   float* loss = nullptr;     // device scalar
+  float* loss_part = nullptr; // per-warp loss partials [ceil(B*Z / 32)]
+  float* wpart = nullptr;    // weight-gradient partials [B * Wd/128][C*C*9 + C]
   SelectState* sel = nullptr; // median selection state
   float* scale = nullptr;    // ln 2 / median |A|^2
   int* status = nullptr;     // bit 0: a bounded wait of the inference kernel gave up
@@ -816,8 +847,9 @@ struct fdas_zband {
 
 namespace {
 void free_zband(fdas_zband* z) {
-  void* ptrs[] = {z->p,  z->ph,     z->g,   z->m,      z->v,    z->a1,   z->a2,      z->a3,    z->d1,
-                  z->d2, z->pooled, z->arg, z->logits, z->dlog, z->loss, z->sel, z->scale, z->status};
+  void* ptrs[] = {z->p,      z->ph,  z->g,      z->m,    z->v,         z->a1,     z->a2,
+                  z->a3,     z->d1,  z->d2,     z->pooled, z->arg,    z->logits, z->dlog,
+                  z->loss,   z->loss_part, z->wpart, z->sel, z->scale, z->status};
   for (void* q : ptrs) cudaFree(q);
   if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
   if (z->graph) cudaGraphDestroy(z->graph);
@@ -918,6 +950,8 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
             cudaMalloc(&z->pooled, B * kC * 4) == cudaSuccess && cudaMalloc(&z->arg, B * kC * 4) == cudaSuccess &&
             cudaMalloc(&z->logits, B * (size_t)n_out * 4) == cudaSuccess &&
             cudaMalloc(&z->dlog, B * (size_t)n_out * 4) == cudaSuccess && cudaMalloc(&z->loss, 4) == cudaSuccess &&
+            cudaMalloc(&z->loss_part, (B * (size_t)n_out + 31) / 32 * 4) == cudaSuccess &&
+            cudaMalloc(&z->wpart, B * (size_t)(window / kTile) * ((size_t)kC * kC * kK + kC) * 4) == cudaSuccess &&
             cudaMalloc(&z->sel, sizeof(SelectState)) == cudaSuccess &&
             cudaMalloc(&z->scale, 4) == cudaSuccess && cudaMalloc(&z->status, 4) == cudaSuccess;
   if (!ok || cudaMemset(z->p, 0, P * 4) != cudaSuccess || cudaMemset(z->ph, 0, P * 2) != cudaSuccess ||
@@ -980,23 +1014,29 @@ int fdas_zband_train_step(fdas_zband* z, const float* d_windows, const float* d_
   const Layout& L = z->lay;
   const int B = batch, Wd = z->Wd, Z = z->Z, P = L.total;
   if (forward(z, d_windows, B, false, st) != cudaSuccess) return FDAS_ERR_CUDA;
-  cudaMemsetAsync(z->loss, 0, 4, st);
-  cudaMemsetAsync(z->g, 0, (size_t)P * 4, st);
-  bce_grad_kernel<<<(B * Z + 255) / 256, 256, 0, st>>>(z->logits, d_targets, B * Z, z->dlog, z->loss);
+  bce_grad_kernel<<<(B * Z + 255) / 256, 256, 0, st>>>(z->logits, d_targets, B * Z, z->dlog, z->loss_part);
+  sum_fixed_kernel<<<1, 1024, 0, st>>>(z->loss_part, (B * Z + 31) / 32, z->loss);
   head_bwd_weights_kernel<<<(Z * (kC + 1) + 255) / 256, 256, 0, st>>>(z->dlog, z->pooled, B, Z, z->g + L.Wl,
                                                                        z->g + L.bl);
   const size_t act = (size_t)B * kC * Wd;
   cudaMemsetAsync(z->d1, 0, act * 4, st);
   head_bwd_data_kernel<<<B, kC, 0, st>>>(z->dlog, z->p + L.Wl, z->arg, z->a3, Z, Wd, z->d1);   // da3
   const dim3 grid(Wd / kTile, B);
-  conv_bwd_weight_kernel<kC, true, kDil3>
-      <<<grid, 256, bwd_weight_smem<kC, kDil3>(), st>>>(z->a2, z->d1, Wd, z->g + L.W3, z->g + L.b3);
+  const int nblk = B * (Wd / kTile);
+  // partials of layer `cin` inputs, then their fixed-order sum into the W and b slices (W then b
+  // are adjacent in the parameter layout)
+  auto reduce = [&](int cin, int w_off) {
+    const int n = kC * cin * kK + kC;
+    reduce_partials_kernel<<<(n + 255) / 256, 256, 0, st>>>(z->wpart, nblk, n, n, z->g + w_off);
+  };
+  conv_bwd_weight_kernel<kC, true, kDil3><<<grid, 256, bwd_weight_smem<kC, kDil3>(), st>>>(z->a2, z->d1, Wd, z->wpart);
+  reduce(kC, L.W3);
   conv_bwd_data_kernel<kDil3><<<grid, 256, bwd_data_smem<kDil3>(), st>>>(z->d1, z->p + L.W3, z->a2, z->d2, Wd);   // da2
-  conv_bwd_weight_kernel<kC, true, kDil2>
-      <<<grid, 256, bwd_weight_smem<kC, kDil2>(), st>>>(z->a1, z->d2, Wd, z->g + L.W2, z->g + L.b2);
+  conv_bwd_weight_kernel<kC, true, kDil2><<<grid, 256, bwd_weight_smem<kC, kDil2>(), st>>>(z->a1, z->d2, Wd, z->wpart);
+  reduce(kC, L.W2);
   conv_bwd_data_kernel<kDil2><<<grid, 256, bwd_data_smem<kDil2>(), st>>>(z->d2, z->p + L.W2, z->a1, z->d1, Wd);   // da1
-  conv_bwd_weight_kernel<1, false, kDil1>
-      <<<grid, 256, bwd_weight_smem<1, kDil1>(), st>>>(d_windows, z->d1, Wd, z->g + L.W1, z->g + L.b1);
+  conv_bwd_weight_kernel<1, false, kDil1><<<grid, 256, bwd_weight_smem<1, kDil1>(), st>>>(d_windows, z->d1, Wd, z->wpart);
+  reduce(1, L.W1);
   z->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)z->step), c2 = 1.f - powf(b2, (float)z->step);
@@ -1160,7 +1200,7 @@ int64_t fdas_zband_work_units_scratch_bytes(int64_t n_groups, int Z) {
 int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
                                  int64_t seg_bins, int G, int h, int64_t n_groups, int32_t* d_units,
                                  uint16_t* d_masks, void* d_scratch, int64_t* host_count, fdas_stream_t stream) {
-  if (!d_logits || !d_units || !host_count || n_windows < 1 || n_windows > (1 << 30) || Z < 1 ||
+  if (!d_logits || !d_units || (!host_count && !d_scratch) || n_windows < 1 || n_windows > (1 << 30) || Z < 1 ||
       !(threshold > 0.f && threshold < 1.f) || hop < 1 || seg_bins < 1 || G < 1 || G > 16 || h < 0 ||
       n_groups < 1 || n_groups > (1 << 24) || (int64_t)n_groups * Z > INT32_MAX ||
       seg_bins * G > (int64_t(1) << 40))
@@ -1184,9 +1224,9 @@ int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z
   scan_counts_kernel<<<1, 1024, 0, st>>>(counts, (int)n_groups, offsets, offsets + n_groups);
   write_units_kernel<<<(unsigned)n_groups, 256, 0, st>>>(masks, offsets, Z, d_units, d_masks);
   int rc = FDAS_OK;
-  if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(host_count, offsets + n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  if (cudaGetLastError() != cudaSuccess) rc = FDAS_ERR_CUDA;
+  else if (host_count && (cudaMemcpyAsync(host_count, offsets + n_groups, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                          cudaStreamSynchronize(st) != cudaSuccess))
     rc = FDAS_ERR_CUDA;
   if (own) cudaFreeAsync(scratch, st);
   return rc;

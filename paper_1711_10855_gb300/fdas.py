@@ -36,7 +36,8 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_zband_work_units", "fdas_zband_destroy", "fdas_convolve_power_tc",
             "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes",
             "fdas_convolve_power_units_masked", "fdas_zband_work_units_masked",
-            "fdas_static_check", "fdas_static_selftest_wait_timeout"]
+            "fdas_static_check", "fdas_static_selftest_wait_timeout",
+            "fdas_convolve_power_units_device_count"]
 
 _lock = threading.Lock()
 _lib = None
@@ -143,6 +144,8 @@ def lib() -> ctypes.CDLL:
             L.fdas_selftest_wait_timeout.restype = i32
             L.fdas_convolve_power_static.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp]
             L.fdas_convolve_power_static.restype = i32
+            L.fdas_convolve_power_units_device_count.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+            L.fdas_convolve_power_units_device_count.restype = i32
             L.fdas_static_check.argtypes = [vp]
             L.fdas_static_check.restype = i32
             L.fdas_static_selftest_wait_timeout.argtypes = [i64, vp]
@@ -256,6 +259,17 @@ class Plan:
             _check(lib().fdas_convolve_power_units_masked(self._h, _ptr(spectrum), _ptr(plane), _ptr(units),
                                                           _ptr(masks), int(n_units), _stream(stream)),
                    "fdas_convolve_power_units_masked")
+
+    def convolve_power_units_device_count(self, spectrum, plane, units, count_ptr: int, max_units: int,
+                                          stream=None, masks=None):
+        """As convolve_power_units with the list length read on the device at address count_ptr
+        (an int64, e.g. the one zband_work_units(..., host_count=False) leaves in its scratch);
+        max_units: the capacity of units (and masks)."""
+        _check(lib().fdas_convolve_power_units_device_count(self._h, _ptr(spectrum), _ptr(plane), _ptr(units),
+                                                            None if masks is None else _ptr(masks),
+                                                            ctypes.c_void_p(int(count_ptr)), int(max_units),
+                                                            _stream(stream)),
+               "fdas_convolve_power_units_device_count")
 
     def template_taps(self, z_idx: int) -> np.ndarray:
         out = np.empty(2 * (self.tmpl_len + 1), dtype=np.float64)
@@ -394,27 +408,38 @@ def zband_work_units_scratch_bytes(n_groups: int, n_z: int) -> int:
 
 
 def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: int, group_bins: int, h: int,
-                     n_groups: int, units, stream=None, scratch=None, masks=None, segments: int = 1) -> int:
+                     n_groups: int, units, stream=None, scratch=None, masks=None, segments: int = 1,
+                     host_count: bool = True):
     """Async work list into `units`; returns its length (synchronises the stream).  `scratch`: a
     device buffer of zband_work_units_scratch_bytes bytes reused across calls (None: allocated
     inside the call).  With `masks` (16-bit device tensor, room for n_groups * n_z), each listed
-    unit's bits for its `segments` segments of group_bins / segments bins."""
-    if masks is not None or segments != 1:
+    unit's bits for its `segments` segments of group_bins / segments bins.  host_count=False (with
+    a scratch): no synchronisation, returns None; the length stays in the scratch at int64 index
+    n_groups (zband_work_units_count_ptr)."""
+    if not host_count and scratch is None:
+        raise ValueError("host_count=False needs a caller scratch")
+    if masks is not None or segments != 1 or not host_count:
         if group_bins % segments:
             raise ValueError("group_bins must be a multiple of segments")
         count = ctypes.c_int64(0)
         _check(lib().fdas_zband_work_units_masked(_ptr(logits), int(n_windows), int(n_z), float(threshold),
                                                   int(hop), int(group_bins // segments), int(segments), int(h),
                                                   int(n_groups), _ptr(units), None if masks is None else _ptr(masks),
-                                                  None if scratch is None else _ptr(scratch), ctypes.byref(count),
+                                                  None if scratch is None else _ptr(scratch),
+                                                  ctypes.byref(count) if host_count else None,
                                                   _stream(stream)), "fdas_zband_work_units_masked")
-        return count.value
+        return count.value if host_count else None
     count = ctypes.c_int64(0)
     _check(lib().fdas_zband_work_units(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(hop),
                                        int(group_bins), int(h), int(n_groups), _ptr(units),
                                        None if scratch is None else _ptr(scratch), ctypes.byref(count),
                                        _stream(stream)), "fdas_zband_work_units")
     return count.value
+
+
+def zband_work_units_count_ptr(scratch, n_groups: int) -> int:
+    """Device address of the list length a work-list call left in `scratch`."""
+    return _ptr(scratch) + 8 * int(n_groups)
 
 
 def _i64_array(values):

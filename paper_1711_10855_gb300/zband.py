@@ -222,6 +222,25 @@ class ProposalSearch:
             self.plan.convolve_power_units(spectrum, plane, self.units, n, masks=self.masks)
         return n
 
+    def search_async(self, spectrum, plane, threshold: float, stream=None) -> None:
+        """As search, without any host synchronisation: the work list's length stays on the device
+        and the correlation reads it there (read it afterwards with device_units())."""
+        self.net.propose(spectrum, self.plan.n_bins, self.logits, stream)
+        fdas.zband_work_units(self.logits, self.n_blocks, self.plan.n_z, threshold, HOP, self.G * self.plan.valid,
+                              self.plan.tmpl_len // 2, self.n_groups, self.units, stream=stream, scratch=self.scratch,
+                              masks=self.masks, segments=self.G if self.masks is not None else 1, host_count=False)
+        self.plan.convolve_power_units_device_count(spectrum, plane, self.units,
+                                                    fdas.zband_work_units_count_ptr(self.scratch, self.n_groups),
+                                                    self.n_groups * self.plan.n_z, stream, masks=self.masks)
+        self.n_units = None
+
+    def device_units(self) -> int:
+        """Length of the last list made on the device (synchronises the current stream)."""
+        import torch
+        cnt = self.scratch[8 * self.n_groups:8 * self.n_groups + 8].view(torch.int64)
+        self.n_units = int(cnt.item())
+        return self.n_units
+
     @property
     def unit_fraction(self) -> float:
         return self.n_units / float(self.n_groups * self.plan.n_z)

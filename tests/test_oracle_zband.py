@@ -188,3 +188,146 @@ def test_work_unit_masks_hand_case_and_group_flags():
     u2, m2 = zband.work_unit_masks(lg, 0.3, 512, 1536 * 8, 1, 256, 4)
     np.testing.assert_array_equal(u1, u2)
     assert np.all(m2 == 1)
+
+
+# ---- running error bounds (the tolerances of the GPU tests of the network) -----------------
+
+def _bound_case(Z=21, W=512, B=6, seed=7):
+    rng = np.random.default_rng(seed)
+    p = zband.init_params(Z, seed=seed, channels=32)
+    for k in ("b1", "b2", "b3", "bl"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.2
+    # a spectrum with chirp-like structure: noise power plus a few broad bumps
+    n = W * (B + 1) // 2 + W
+    pw = rng.exponential(1.0, n)
+    for c in rng.integers(W // 2, n - W // 2, 3):
+        pw[c - 40:c + 40] += rng.uniform(5, 20)
+    x = zband.windows(np.minimum(pw, zband.X_CAP), W, W // 2, B)
+    return p, x
+
+
+def _f16(p):
+    return {k: v.astype(np.float16).astype(np.float64) for k, v in p.items()}
+
+
+def _emulate_fp16_kernel(p16, x):
+    """The inference kernel's rounding in numpy: x and layer-1/2 activations in FP16, sums in
+    FP32 (any order), layer 3 max-pooled in FP32, head in FP32."""
+    f32 = np.float32
+    h = x.astype(f32).astype(np.float16).astype(f32)[:, None, :]
+    for layer in range(3):
+        W = p16[f"W{layer + 1}"].astype(f32)
+        b = p16[f"b{layer + 1}"].astype(f32)
+        d = zband.DIL[layer]
+        B, I, T = h.shape
+        P = zband.PAD * d
+        hp = np.zeros((B, I, T + 2 * P), dtype=f32)
+        hp[:, :, P:P + T] = h
+        a = np.zeros((B, W.shape[0], T), dtype=f32)
+        for k in range(zband.K):
+            a = (a + np.einsum("oi,bit->bot", W[:, :, k], hp[:, :, k * d:k * d + T])).astype(f32)
+        a = (a + b[None, :, None]).astype(f32)
+        h = np.maximum(a, f32(0))
+        if layer < 2:
+            h = h.astype(np.float16).astype(f32)
+    T = h.shape[2]
+    m = h[:, :, T // 4:3 * T // 4].max(axis=2)
+    return (m @ p16["Wl"].astype(f32).T + p16["bl"].astype(f32)[None, :]).astype(np.float64)
+
+
+FP16_MODEL = dict(x_u=zband.U16 + 8 * zband.U32, act_u=zband.U16, acc_u=2.0 ** -23, head_u=zband.U32)
+
+
+def test_logits_bound_covers_an_fp16_emulation_and_is_tight():
+    """The inference kernel's rounding, emulated in numpy (FP16 input and activations, FP32 sums),
+    stays inside the bound; the bound is a few times the emulated error, not the logits' scale."""
+    p, x = _bound_case()
+    p16 = _f16(p)
+    logits, bound = zband.logits_error_bound(p16, x, **FP16_MODEL)
+    emu = _emulate_fp16_kernel(p16, x)
+    err = np.abs(emu - logits)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.max(bound) < 5e-3 * np.abs(logits).max()
+    assert np.median(bound / np.maximum(err, 1e-300)) < 100.0
+
+
+def _planted(p, x, mode):
+    """The exact network with one planted mistake (for the detection test only)."""
+    h0 = np.asarray(x, dtype=np.float64)[:, None, :]
+    dil = list(zband.DIL)
+    W2 = p["W2"].copy()
+    if mode == "dilation":
+        dil[2] = 15                                    # layer 3 with the wrong tap spacing
+    if mode == "tap":
+        W2[:, :, 8] = 0.0                              # a dropped tap
+    h1 = np.maximum(zband.conv_k9(h0, p["W1"], p["b1"], dil[0]), 0.0)
+    if mode == "halo":
+        h1 = np.concatenate([h1[:, :, 1:], np.zeros_like(h1[:, :, :1])], axis=2)   # one-row shift
+    h2 = np.maximum(zband.conv_k9(h1, W2, p["b2"], dil[1]), 0.0)
+    h3 = np.maximum(zband.conv_k9(h2, p["W3"], p["b3"], dil[2]), 0.0)
+    T = h3.shape[2]
+    m = h3[:, :, T // 4:3 * T // 4].max(axis=2)
+    return m @ p["Wl"].T + p["bl"][None, :]
+
+
+@pytest.mark.parametrize("mode", ["halo", "dilation", "tap"])
+def test_forward_bound_detects_planted_layer_errors(mode):
+    """A one-row halo shift, a wrong dilation or a dropped tap moves logits by far more than the
+    bound: the tolerance of the inference test would catch each."""
+    p, x = _bound_case()
+    p16 = _f16(p)
+    logits, bound = zband.logits_error_bound(p16, x, **FP16_MODEL)
+    bad = _planted(p16, x, mode)
+    assert np.max(np.abs(bad - logits) / bound) > 3.0
+
+
+def _emulate_fp32_training_grads(p, x, tgt):
+    """FP32 storage of every intermediate of the oracle's forward and backward (values rounded to
+    FP32 after each exact operation): an implementation within the rounding model."""
+    r = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    pr = {k: r(v) for k, v in p.items()}
+    h0 = r(x)[:, None, :]
+    a1 = r(zband.conv_k9(h0, pr["W1"], pr["b1"], zband.DIL[0]))
+    h1 = np.maximum(a1, 0)
+    a2 = r(zband.conv_k9(h1, pr["W2"], pr["b2"], zband.DIL[1]))
+    h2 = np.maximum(a2, 0)
+    a3 = r(zband.conv_k9(h2, pr["W3"], pr["b3"], zband.DIL[2]))
+    h3 = np.maximum(a3, 0)
+    T = h3.shape[2]
+    lo, hi = T // 4, 3 * T // 4
+    arg = np.argmax(h3[:, :, lo:hi], axis=2) + lo
+    m = np.take_along_axis(h3, arg[:, :, None], axis=2)[:, :, 0]
+    logits = r(m @ pr["Wl"].T + pr["bl"][None, :])
+    n = logits.size
+    dlog = r((1.0 / (1.0 + np.exp(-logits)) - tgt) / n)
+    g = {"Wl": r(dlog.T @ m), "bl": r(dlog.sum(axis=0))}
+    dm = r(dlog @ pr["Wl"])
+    B, C, _ = h3.shape
+    da3 = np.zeros_like(h3)
+    da3[np.arange(B)[:, None], np.arange(C)[None, :], arg] = dm
+    da3 = da3 * (a3 > 0)
+    dh2, g["W3"], g["b3"] = zband.conv_k9_backward(h2, pr["W3"], da3, zband.DIL[2])
+    da2 = r(dh2) * (a2 > 0)
+    dh1, g["W2"], g["b2"] = zband.conv_k9_backward(h1, pr["W2"], da2, zband.DIL[1])
+    da1 = r(dh1) * (a1 > 0)
+    _, g["W1"], g["b1"] = zband.conv_k9_backward(h0, pr["W1"], da1, zband.DIL[0])
+    return {k: r(v) for k, v in g.items()}
+
+
+def test_gradient_bound_covers_an_fp32_emulation():
+    p, x = _bound_case(B=8)
+    p = {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
+    x = x.astype(np.float32).astype(np.float64)
+    tgt = (np.random.default_rng(3).random((x.shape[0], p["Wl"].shape[0])) < 0.2).astype(np.float64)
+    g, bnd = zband.grads_error_bound(p, x, tgt)
+    emu = _emulate_fp32_training_grads(p, x, tgt)
+    for k in g:
+        err = np.abs(emu[k] - g[k])
+        assert np.all(err <= bnd[k] + 1e-30), (k, float(np.max(err / (bnd[k] + 1e-30))))
+        # small against each tensor's scale: far below the head and layer-3 gradients' scale, and
+        # in the median below 5e-3 of it everywhere (entries fed by a relu mask within lam sigma
+        # of flipping carry that branch's whole term)
+        scale = np.abs(g[k]).max()
+        if k in ("Wl", "bl", "W3", "b3"):
+            assert np.max(bnd[k]) <= 1e-3 * scale, (k, float(np.max(bnd[k]) / scale))
+        assert np.median(bnd[k]) <= 5e-3 * scale, (k, float(np.median(bnd[k]) / scale))
