@@ -295,6 +295,22 @@ def run_batch(args):
         "gpu_launches": args.steps * (1 if best in (512, 2048) else int(args.batch_count)),
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
+    # parity of this workload at full size: tests/test_gpu_batch_scale.py
+    if not args.no_cpu_baseline:
+        cores = cpu_cores()
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        import oracle
+        i_big = int(np.argmax(n_bins))
+        spec_big = specs[i_big].cpu().numpy().view(np.complex64)
+        t0, rows = time.time(), 0
+        while time.time() - t0 < args.cpu_seconds and rows < int(n_z[i_big]):
+            oracle.plane_rows(spec_big, int(zmax[i_big]), zstep, m, rows, rows + 1)
+            rows += 1
+        dt = time.time() - t0
+        line["cpu_baseline"] = {"value": rows * int(n_bins[i_big]) / dt, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{rows} whole rows ({rows * int(n_bins[i_big])} cells) of the largest "
+                                          f"spectrum's plane, FP64 direct sum, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
     b.close()
     return 0

@@ -426,3 +426,14 @@ def test_device_count_path_matches_host_count_path():
             plan.check()
         assert e.value.code == fdas.FDAS_ERR_INVALID
         assert torch.isnan(c).all()
+        # a negative count is rejected the same way; an empty list computes nothing and is valid
+        for count, ok in ((-1, False), (0, True)):
+            cnt = torch.tensor([count], dtype=torch.int64, device="cuda")
+            plan.convolve_power_units_device_count(spec, c, ps.units, cnt.data_ptr(), ps.n_groups * plan.n_z,
+                                                   masks=ps.masks)
+            if ok:
+                plan.check()
+            else:
+                with pytest.raises(fdas.FdasError):
+                    plan.check()
+            assert torch.isnan(c).all()
