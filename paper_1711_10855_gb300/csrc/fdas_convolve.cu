@@ -697,12 +697,12 @@ __global__ void __launch_bounds__(256, 1)
       if (i < bpos) fetch(i);
       while (i < bpos) {
         const int ok = __all_sync(0xffffffffu, wait_slot(&wbar[warp], w_phase, abort_flag));
-        w_in_flight = false;
-        w_phase ^= 1u;
-        if (!ok) {
+        if (!ok) {   // the copy stays in flight: the exit path waits for it (bounded)
           if (lane == 0) report_timeout(p.status, abort_flag);
           break;
         }
+        w_in_flight = false;
+        w_phase ^= 1u;
         const int64_t z = unit_at(u0 + i) % d.Z;
         const int lim_z = ((warp_bits(i) >> gw) & 1u) ? lim : 0;
         const float4* st4 = reinterpret_cast<const float4*>(myRegion);
