@@ -224,6 +224,7 @@ int fdas_batch_convolve_power(fdas_batch* batch, const float* const* d_spectra, 
 
 /* As fdas_check for the batch's status word. */
 int fdas_batch_check(fdas_batch* batch, fdas_stream_t stream);
+/* Waits for the batch's last enqueued work (not the whole device), then frees it. */
 int fdas_batch_destroy(fdas_batch* batch);
 /* seg_len, template-bank rows, total work units, segments resident per CTA (0: one launch per
  * spectrum); NULL outputs skipped. */
@@ -274,6 +275,31 @@ int fdas_convolve_power_units_device_count(fdas_plan* plan, const float* d_spect
                                            int64_t max_units, fdas_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Pair lists (seg_len 2048 only; the paper has no counterpart).  A pair is s*Z + z: segment s
+ * (outputs [s*V, (s+1)*V), fed by the input bins [s*V - m/2, s*V - m/2 + seg_len)) and template
+ * z_idx.  fdas_convolve_power_pairs computes only the listed pairs (ascending, device int32
+ * array, 4-byte aligned) and writes only their cells: row z of the bins [s*V, min((s+1)*V, n))
+ * of each listed (s, z); every other cell of d_plane is left untouched.  Each cell equals the one
+ * fdas_convolve_power writes (the same transforms, Section 2 and Eq. 2-3).  The list is cut into
+ * equal contiguous ranges, one per warp of the grid, so a sparse list costs about its share of the
+ * full plane's transforms however its pairs are spread over segments and templates (each warp
+ * also runs the forward transform of every segment its range enters).  The list is checked on
+ * the device (strictly increasing, every entry in [0, nseg*Z)); a list that fails is not run and
+ * the next fdas_check() returns FDAS_ERR_INVALID.  Asynchronous, no allocation.  FDAS_ERR_INVALID
+ * for NULL pointers, n_pairs < 1 or a plan whose seg_len is not 2048; FDAS_ERR_ALIGN for
+ * misaligned pointers; FDAS_ERR_NOT_BUILT before fdas_templates_build.
+ * ------------------------------------------------------------------------------------------- */
+int fdas_convolve_power_pairs(fdas_plan* plan, const float* d_spectrum, float* d_plane, const int32_t* d_pairs,
+                              int64_t n_pairs, fdas_stream_t stream);
+/* As fdas_convolve_power_pairs with the list length read on the device from *d_count (int64,
+ * 8-byte aligned: e.g. the length fdas_zband_work_pairs leaves in its workspace); max_pairs >= 1
+ * is the capacity of d_pairs, and a *d_count outside [0, max_pairs] fails the device-side check
+ * like a bad list. */
+int fdas_convolve_power_pairs_device_count(fdas_plan* plan, const float* d_spectrum, float* d_plane,
+                                           const int32_t* d_pairs, const int64_t* d_count, int64_t max_pairs,
+                                           fdas_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Learned z-band proposal (no counterpart in the paper): a 1-D convolutional network over the
  * z = 0 power spectrum (the plane's z = 0 row, Eq. 2 with the unit-impulse template) that
  * predicts, for each block of bins, which of Z templates are worth correlating there.
@@ -302,11 +328,13 @@ typedef struct fdas_zband fdas_zband;
 fdas_zband* fdas_zband_create(int window, int n_out, int max_batch);
 int fdas_zband_param_count(const fdas_zband* net);
 /* Host copies of the FP32 parameters (param_count floats).  Setting refreshes the FP16 copy and
- * resets Adam (moments zero, step 0).  Both synchronise the device. */
+ * resets Adam (moments zero, step 0).  Both wait for the net's own last enqueued work (train
+ * steps, predictions, proposals, on whatever stream) and return when the copy is complete; they
+ * do not synchronise the device. */
 int fdas_zband_set_params(fdas_zband* net, const float* host_params);
 int fdas_zband_get_params(fdas_zband* net, float* host_params);
 /* Adam state for checkpoints: first and second moments (param_count floats each) and the step
- * count.  Set after fdas_zband_set_params to resume training.  Synchronise the device. */
+ * count.  Set after fdas_zband_set_params to resume training.  Wait as fdas_zband_get_params. */
 int fdas_zband_get_adam(fdas_zband* net, float* host_m, float* host_v, int* host_step);
 int fdas_zband_set_adam(fdas_zband* net, const float* host_m, const float* host_v, int step);
 /* One Adam step (lr > 0; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on `batch` windows of
@@ -315,7 +343,7 @@ int fdas_zband_set_adam(fdas_zband* net, const float* host_m, const float* host_
  * synchronising `stream`).  Asynchronous otherwise. */
 int fdas_zband_train_step(fdas_zband* net, const float* d_windows, const float* d_targets, int batch, float lr,
                           float* host_loss, fdas_stream_t stream);
-/* Gradients of the last train step (host, param_count floats; synchronises the device). */
+/* Gradients of the last train step (host, param_count floats; waits as fdas_zband_get_params). */
 int fdas_zband_gradients(fdas_zband* net, float* host_grads);
 /* Logits (device, batch x Z) for windows of x on the CUDA cores (FP32 activations);
  * half_weights != 0 uses the FP16 copy of the parameters. */
@@ -365,6 +393,20 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
 int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
                                  int64_t seg_bins, int G, int h, int64_t n_groups, int32_t* d_units,
                                  uint16_t* d_masks, void* d_scratch, int64_t* host_count, fdas_stream_t stream);
+/* Pair list from block logits (device, n_windows x Z), for fdas_convolve_power_pairs: pair
+ * s*Z + z is listed when some template z' with |z' - z| <= z_halo (0 <= z_halo <= Z) has
+ * sigmoid(logit) >= threshold (0 < threshold < 1) in a block w whose bins [w*hop, (w+1)*hop)
+ * meet [s*seg_bins - h, (s+1)*seg_bins + h) (seg_bins = V).  z_halo widens each proposal by
+ * z_halo templates on both sides, for signals whose template the network places only roughly.
+ * Writes the ascending list to d_pairs (room for n_seg*Z int32; n_seg*Z <= 2^31 - 1, Z <= 8192)
+ * and its length to *host_count (synchronises `stream`), or with host_count NULL leaves it on
+ * the device as the int64 at ((const int64_t*)d_scratch)[n_seg].  d_scratch: 16-byte aligned
+ * caller workspace of fdas_zband_work_units_scratch_bytes(n_seg, Z) bytes (required).
+ * Asynchronous when host_count is NULL; three launches, no allocation. */
+int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, int z_halo, int hop,
+                          int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs, void* d_scratch,
+                          int64_t* host_count, fdas_stream_t stream);
+/* Waits for the net's last enqueued work (not the whole device), then frees it. */
 int fdas_zband_destroy(fdas_zband* net);
 
 /*

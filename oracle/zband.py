@@ -25,7 +25,7 @@ inference kernel computes.
 
 Only tests/ import this module.  The GPU implementation (csrc/fdas_zband.cu) shares nothing with it.
 Pins: tests/test_oracle_zband.py (direct sums, finite differences, closed forms of Adam's first
-step, brute-force work lists).
+step, brute-force work lists and pair lists).
 """
 from __future__ import annotations
 
@@ -203,6 +203,25 @@ def work_unit_masks(logits: np.ndarray, threshold: float, hop: int, seg_bins: in
                 units.append(g * Z + z)
                 masks.append(m)
     return np.asarray(units, dtype=np.int64), np.asarray(masks, dtype=np.int64)
+
+
+def work_pairs(logits: np.ndarray, threshold: float, z_halo: int, hop: int, seg_bins: int, h: int,
+               n_seg: int) -> np.ndarray:
+    """Ascending pairs s*Z + z: segment s (outputs [s*V, (s+1)*V), V = seg_bins, input bins
+    reaching h further on each side) is listed for template z when a block w whose bins
+    [w*hop, (w+1)*hop) meet [s*V - h, (s+1)*V + h) has sigmoid(logit[w, z']) >= threshold for
+    some template z' with |z' - z| <= z_halo."""
+    nw, Z = logits.shape
+    keep = 1.0 / (1.0 + np.exp(-np.asarray(logits, dtype=np.float64))) >= threshold
+    pairs = []
+    for s in range(n_seg):
+        lo, hi = s * seg_bins - h, (s + 1) * seg_bins + h
+        blocks = [w for w in range(nw) if w * hop < hi and (w + 1) * hop > lo]
+        for z in range(Z):
+            near = range(max(0, z - z_halo), min(Z, z + z_halo + 1))
+            if any(keep[w, q] for w in blocks for q in near):
+                pairs.append(s * Z + z)
+    return np.asarray(pairs, dtype=np.int64)
 
 
 # ---------------------------------------------------------------------------------------------

@@ -367,7 +367,9 @@ fdas_plan* fdas_plan_create(int64_t n_bins, int zmax, int zstep, int seg_len, in
     g_last_error = FDAS_ERR_ALLOC;
     return nullptr;
   }
-  if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) {
+  // cleared before any stream can use the plan (a non-blocking stream is not ordered after
+  // default-stream work)
+  if (cudaMemsetAsync(p->d_status, 0, sizeof(int), 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) {
     free_plan_memory(p);
     delete p;
     g_last_error = FDAS_ERR_CUDA;
@@ -472,6 +474,46 @@ int fdas_convolve_power_units(fdas_plan* p, const float* d_spectrum, float* d_pl
   return fdas_convolve_power_units_masked(p, d_spectrum, d_plane, d_units, nullptr, n_units, stream);
 }
 
+namespace {
+int convolve_pairs(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_pairs,
+                   const int64_t* d_count, int64_t n_pairs, fdas_stream_t stream) {
+  if (!p || !d_spectrum || !d_plane || !d_pairs || n_pairs < 1) return FDAS_ERR_INVALID;
+  if (!p->built) return FDAS_ERR_NOT_BUILT;
+  if (!fdas::pairs_supported(p->L)) return FDAS_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(d_spectrum) & 15u) || (reinterpret_cast<uintptr_t>(d_plane) & 15u) ||
+      (reinterpret_cast<uintptr_t>(d_pairs) & 3u) || (reinterpret_cast<uintptr_t>(d_count) & 7u))
+    return FDAS_ERR_ALIGN;
+  fdas::PairParams q;
+  q.spec = reinterpret_cast<const float2*>(d_spectrum);
+  q.plane = d_plane;
+  q.templates = p->d_templates;
+  q.twist = p->d_twist;
+  q.status = p->d_status;
+  q.pairs = d_pairs;
+  q.pair_count = d_count;
+  q.n_pairs = n_pairs;
+  q.n_bins = p->n_bins;
+  q.nseg = p->nseg;
+  q.Z = p->Z;
+  q.V = p->V;
+  q.h = p->h;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return enqueued(p, st, fdas::launch_pairs(p->L, q, p->sm_count, st));
+}
+}  // namespace
+
+int fdas_convolve_power_pairs(fdas_plan* p, const float* d_spectrum, float* d_plane, const int32_t* d_pairs,
+                              int64_t n_pairs, fdas_stream_t stream) {
+  return convolve_pairs(p, d_spectrum, d_plane, d_pairs, nullptr, n_pairs, stream);
+}
+
+int fdas_convolve_power_pairs_device_count(fdas_plan* p, const float* d_spectrum, float* d_plane,
+                                           const int32_t* d_pairs, const int64_t* d_count, int64_t max_pairs,
+                                           fdas_stream_t stream) {
+  if (!d_count) return FDAS_ERR_INVALID;
+  return convolve_pairs(p, d_spectrum, d_plane, d_pairs, d_count, max_pairs, stream);
+}
+
 int fdas_segment_spectra(fdas_plan* p, const float* d_spectrum, float* d_out, fdas_stream_t stream) {
   if (!p || !d_spectrum || !d_out) return FDAS_ERR_INVALID;
   if (!p->built) return FDAS_ERR_NOT_BUILT;
@@ -572,11 +614,15 @@ int fdas_segment_spectra_tc(fdas_plan* p, const float* d_spectrum, float* d_out,
 
 int fdas_check(fdas_plan* p, fdas_stream_t stream) {
   if (!p) return FDAS_ERR_INVALID;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int status = 0;
-  if (cudaMemcpy(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
   if (status != 0) {
-    cudaMemset(p->d_status, 0, sizeof(int));
+    // cleared in the stream's order, before the call returns
+    if (cudaMemsetAsync(p->d_status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
     return (status & fdas::kStatusTimeout) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
   }
   return FDAS_OK;

@@ -36,6 +36,9 @@ struct fdas_batch {
   cudaStream_t capture_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // completion of the last work this batch enqueued (fdas_batch_destroy waits on it, not on the
+  // whole device)
+  cudaEvent_t done = nullptr;
   // per-spectrum launches (G == 0): the pointers the graph was captured with
   std::vector<const float*> cap_specs;
   std::vector<float*> cap_planes;
@@ -49,6 +52,7 @@ void free_batch(fdas_batch* b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->done) cudaEventDestroy(b->done);
   cudaFree(b->d_templates);
   cudaFree(b->d_taps);
   cudaFree(b->d_twist);
@@ -56,6 +60,16 @@ void free_batch(fdas_batch* b) {
   cudaFree(b->d_descs);
   if (b->h_descs) cudaFreeHost(b->h_descs);
   delete b;
+}
+
+// Record the batch's completion event after work enqueued on `st` (not while `st` is being
+// captured into a CUDA graph: a captured record is no event the host can wait on).
+int note_work(fdas_batch* b, cudaStream_t st, cudaError_t launch) {
+  if (launch != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return FDAS_OK;
+  return cudaEventRecord(b->done, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 fdas::BatchParams batch_params(const fdas_batch* b) {
@@ -176,8 +190,9 @@ fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax,
     g_batch_error = FDAS_ERR_ALLOC;
     return nullptr;
   }
-  if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaMemsetAsync(b->d_status, 0, sizeof(int), 0) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
     free_batch(b);
     g_batch_error = FDAS_ERR_CUDA;
     return nullptr;
@@ -201,9 +216,10 @@ fdas_batch* fdas_batch_create(int count, const int64_t* n_bins, const int* zmax,
 
 int fdas_batch_templates_build(fdas_batch* b, fdas_stream_t stream) {
   if (!b) return FDAS_ERR_INVALID;
-  if (fdas::build_templates_into(b->d_taps, b->d_templates, b->d_twist, b->zmax_bank, b->zstep, b->L, b->m,
-                                 reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int rc = note_work(
+      b, st, fdas::build_templates_into(b->d_taps, b->d_templates, b->d_twist, b->zmax_bank, b->zstep, b->L, b->m, st));
+  if (rc != FDAS_OK) return rc;
   b->built = true;
   return FDAS_OK;
 }
@@ -227,7 +243,7 @@ int fdas_batch_convolve_power(fdas_batch* b, const float* const* d_spectra, floa
   if (b->G > 0 && cudaMemcpyAsync(b->d_descs, b->h_descs, sizeof(fdas::SpecDesc) * (size_t)b->count,
                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
     return FDAS_ERR_CUDA;
-  if (!use_graph) return launch_any(b, d_spectra, d_planes, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  if (!use_graph) return note_work(b, st, launch_any(b, d_spectra, d_planes, st));
   if (b->G == 0 && b->graph_exec &&
       (!std::equal(b->cap_specs.begin(), b->cap_specs.end(), d_spectra) ||
        !std::equal(b->cap_planes.begin(), b->cap_planes.end(), d_planes))) {
@@ -258,16 +274,19 @@ int fdas_batch_convolve_power(fdas_batch* b, const float* const* d_spectra, floa
     b->cap_specs.assign(d_spectra, d_spectra + b->count);
     b->cap_planes.assign(d_planes, d_planes + b->count);
   }
-  return cudaGraphLaunch(b->graph_exec, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return note_work(b, st, cudaGraphLaunch(b->graph_exec, st));
 }
 
 int fdas_batch_check(fdas_batch* b, fdas_stream_t stream) {
   if (!b) return FDAS_ERR_INVALID;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int status = 0;
-  if (cudaMemcpy(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
   if (status != 0) {
-    cudaMemset(b->d_status, 0, sizeof(int));
+    if (cudaMemsetAsync(b->d_status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
     return FDAS_ERR_TIMEOUT;
   }
   return FDAS_OK;
@@ -275,7 +294,7 @@ int fdas_batch_check(fdas_batch* b, fdas_stream_t stream) {
 
 int fdas_batch_destroy(fdas_batch* b) {
   if (!b) return FDAS_OK;
-  cudaDeviceSynchronize();
+  if (b->done) cudaEventSynchronize(b->done);   // the batch's last enqueued work, not the whole device
   free_batch(b);
   return FDAS_OK;
 }

@@ -835,6 +835,197 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
 }
 
+// Pair-list kernel (one transform per warp, L = 2048).  The listed (segment s, template z) pairs,
+// entries s*Z + z in ascending order, are cut into equal contiguous ranges, one per warp of the
+// grid, so a sparse list costs about its share of the full plane's transforms whatever its
+// layout.  The warps are independent: a warp whose range enters a new segment brings it into its
+// shared region (bulk copy of the part inside [0, n), zero fill of the rest) and runs the forward
+// transform (Eq. 3) into its TMEM columns; for every pair it brings the template into the same
+// region (bulk copy, issued as soon as the previous transform's exchange tile has been read when
+// the next pair has the same segment), multiplies, runs the inverse transform and stores |y|^2
+// for the segment's valid outputs (Section 2, overlap-and-save).  One mbarrier per warp serves
+// both kinds of copy, at most one of them in flight.
+template <class Cfg, int NV>
+__global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairParams p) {
+  static_assert(Cfg::F == 1, "one transform per warp");
+  constexpr int L = Cfg::L, N1 = Cfg::N1, H2 = Cfg::H2, W = Cfg::W;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + (size_t)W * Cfg::REGION);   // [W]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(wbar + W);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + W) + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, k1 = lane;
+  float2* myRegion = reinterpret_cast<float2*>(smem + (size_t)warp * Cfg::REGION);
+  float4* myXb = reinterpret_cast<float4*>(myRegion);
+  uint64_t* bar = &wbar[warp];
+
+  // a list that failed its check (kStatusBadList, set by the preceding check kernel) is not run
+  if (*reinterpret_cast<volatile const int*>(p.status) & kStatusBadList) return;
+  const int64_t P = p.pair_count ? *p.pair_count : p.n_pairs;
+  const int64_t NW = (int64_t)gridDim.x * W;
+  const int64_t cta0 = (int64_t)blockIdx.x * W;
+  if ((cta0 + W) * P / NW == cta0 * P / NW) return;   // no pair for this CTA (uniform)
+  const int64_t e0 = (cta0 + warp) * P / NW, e1 = (cta0 + warp + 1) * P / NW;
+
+  if (tid == 0) {
+    for (int w = 0; w < W; ++w) mbar_init(&wbar[w], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tmem_row = *tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t tw_addr = tmem_row + Cfg::COL_TW;
+  const uint32_t x_addr = tmem_row + Cfg::COL_X + (uint32_t)(warp >> 2) * (2 * Cfg::N2);
+  // twiddle pairs of lane k1 into this quadrant's TMEM rows (one warp per quadrant)
+  if (warp < 4) {
+    const float4* tw4 = reinterpret_cast<const float4*>(p.twist);
+    static_for<H2 / 4>([&](auto cc) {
+      constexpr int c = decltype(cc)::value;
+      float r[16];
+      static_for<4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+        const float4 w = __ldg(tw4 + (4 * c + q) * N1 + k1);
+        r[4 * q] = w.x;
+        r[4 * q + 1] = w.y;
+        r[4 * q + 2] = w.z;
+        r[4 * q + 3] = w.w;
+      });
+      tmem_st16(tw_addr + 16 * c, r);
+    });
+    tmem_wait_st();
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+
+  uint32_t phase = 0;
+  bool in_flight = false;   // a copy into this warp's region not yet waited for (warp-uniform)
+  // bounded wait for the copy in flight; false after a timeout (the copy stays marked in flight)
+  auto wait_copy = [&]() -> bool {
+    const int ok = __all_sync(0xffffffffu, wait_slot(bar, phase, abort_flag));
+    if (!ok) {
+      if (lane == 0) report_timeout(p.status, abort_flag);
+      return false;
+    }
+    in_flight = false;
+    phase ^= 1u;
+    return true;
+  };
+  // template z into the region (its earlier generic accesses are ordered before the copy)
+  auto fetch_template = [&](int z) {
+    __syncwarp();
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, L * 8);
+      bulk_g2s(myRegion, p.templates + (size_t)z * L, L * 8, bar);
+    }
+    in_flight = true;
+  };
+
+  int64_t cur_s = -1;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int32_t u = __ldg(p.pairs + e);
+    const int64_t s = u / p.Z;
+    const int z = (int)(u - s * p.Z);
+    if (s != cur_s) {
+      // a2: the segment's window A[sV - h, sV - h + L): bulk copy of its part inside [0, n) (even
+      // bounds: n and h are multiples of 4, so every copy is whole 16-byte units), zeros elsewhere
+      const int64_t x0 = s * (int64_t)p.V - p.h;
+      const int64_t c0 = x0 > 0 ? x0 : 0;
+      const int64_t c1 = x0 + L < p.n_bins ? x0 + L : p.n_bins;
+      __syncwarp();
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)((c1 - c0) * 8));
+        bulk_g2s(myRegion + (c0 - x0), p.spec + c0, (uint32_t)((c1 - c0) * 8), bar);
+      }
+      in_flight = true;
+      for (int i = k1; i < L; i += N1)
+        if (x0 + i < c0 || x0 + i >= c1) myRegion[i] = make_float2(0.f, 0.f);
+      if (!wait_copy()) break;
+      __syncwarp();
+      // a3: forward FFT of the segment; X pairs (k2 = 2p, 2p+1) go to TMEM
+      float xr[16];
+      forward_transform_with<Cfg>(
+          myRegion, [&](cp2 (&v)[H2]) { apply_twist_tmem<Cfg, true>(v, tw_addr); }, myXb, k1,
+          [&](auto, auto nn, const cp2& x) {
+            constexpr int n1 = decltype(nn)::value;
+            xr[4 * (n1 & 3)] = x.re.x;
+            xr[4 * (n1 & 3) + 1] = x.re.y;
+            xr[4 * (n1 & 3) + 2] = x.im.x;
+            xr[4 * (n1 & 3) + 3] = x.im.y;
+            if constexpr ((n1 & 3) == 3) tmem_st16(x_addr + 4 * (n1 - 3), xr);
+          });
+      tmem_wait_st();
+      cur_s = s;
+      fetch_template(z);
+    }
+    if (!wait_copy()) break;
+    // the next pair's template is fetched during this transform when it has the same segment
+    int znext = -1;
+    if (e + 1 < e1) {
+      const int32_t un = __ldg(p.pairs + e + 1);
+      if ((int64_t)un / p.Z == s) znext = (int)(un - s * p.Z);
+    }
+    // a4: Y = X (TMEM) * T (this warp's region), packed pairs in bit-reversed order
+    const float4* st4 = reinterpret_cast<const float4*>(myRegion);
+    cp2 v[H2];
+    static_for<H2 / 4>([&](auto cc) {
+      constexpr int c = decltype(cc)::value;
+      float x0[16];
+      tmem_ld16(x_addr + 16 * c, x0);
+      float4 t[4];
+      static_for<4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+        t[q] = st4[(4 * c + q) * N1 + k1];
+      });
+      tmem_wait_ld();
+      static_for<4>([&](auto qq) {
+        constexpr int q = decltype(qq)::value;
+        constexpr int pp = 4 * c + q;
+        const cp2 x = cp2{make_float2(x0[4 * q], x0[4 * q + 1]), make_float2(x0[4 * q + 2], x0[4 * q + 3])};
+        v[bitrev(2 * pp, Cfg::LOG_N2)] = cmul2(x, cp2_from(t[q]));
+      });
+    });
+    // a5: inverse FFT; a6 + a7: keep n < V inside the spectrum, store |y|^2
+    fft_split_pairs<Cfg::N2, +1>(v);
+    apply_twist_tmem<Cfg, false>(v, tw_addr);
+    const int64_t segbase = s * (int64_t)p.V;
+    const int64_t lim64 = p.n_bins - segbase < (int64_t)p.V ? p.n_bins - segbase : (int64_t)p.V;
+    const int lim = (int)lim64;
+    float* row = p.plane + (int64_t)z * p.n_bins + segbase;
+    exchange_and_pass2<Cfg, +1>(
+        v, myXb, k1,
+        [&](auto, auto nn, const cp2& y) {
+          constexpr int n1 = decltype(nn)::value;
+          if constexpr (n1 < NV) {
+            const float2 pw = power2(y);
+            const int n_lo = k1 + Cfg::N2 * n1;
+            const int n_hi = n_lo + N1;
+            if (n_lo < lim) __stcs(row + n_lo, pw.x);
+            if (n_hi < lim) __stcs(row + n_hi, pw.y);
+          }
+        },
+        [&]() {
+          if (znext >= 0) fetch_template(znext);
+        });
+  }
+
+  // a copy still in flight after a timeout: wait for it (bounded); always free TMEM
+  if (lane == 0 && in_flight) (void)mbar_wait(bar, phase);
+  __syncwarp();
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(*tmem_slot, Cfg::TMEM_COLS);
+}
+
 // Forward transforms only (steps a2 + a3), natural-order output, for tests of the FFT.
 template <class Cfg>
 __global__ void __launch_bounds__(256, 1)
@@ -1050,6 +1241,36 @@ cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const
   q.V = p.V;
   q.h = p.h;
   return launch_desc(L, q, sm_count, st);
+}
+
+bool pairs_supported(int L) { return L == 2048; }
+
+template <class Cfg, int NV>
+static cudaError_t launch_pairs_nv(const PairParams& p, int sm_count, cudaStream_t st) {
+  constexpr size_t smem = (size_t)Cfg::W * Cfg::REGION + 128;
+  static_assert(smem <= 232448, "shared memory budget of the pair-list kernel");
+  auto kern = fdas_convolve_pairs_kernel<Cfg, NV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // every SM when the length is on the device; otherwise no more CTAs than W-pair shares
+  const int64_t need = (p.n_pairs + Cfg::W - 1) / Cfg::W;
+  const int64_t grid = p.pair_count || need > sm_count ? sm_count : need;
+  kern<<<(unsigned)grid, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(int L, const PairParams& p, int sm_count, cudaStream_t st) {
+  if (!pairs_supported(L) || p.n_pairs < 1) return cudaErrorInvalidValue;
+  {
+    const int64_t blocks = (p.n_pairs + 255) / 256;
+    const unsigned grid = (unsigned)(blocks < 4LL * sm_count ? blocks : 4LL * sm_count);
+    check_units_kernel<<<grid, 256, 0, st>>>(p.pairs, p.n_pairs, p.nseg * p.Z, p.status, p.pair_count);
+  }
+  // two instantiations (compile time): rows pruned to 3/4 (m >= L/4), or none pruned
+  using Cfg = TmemCfg<2048, 32>;
+  const int rows = (p.V + Cfg::N2 - 1) / Cfg::N2;
+  if (rows <= Cfg::N1 * 3 / 4) return launch_pairs_nv<Cfg, Cfg::N1 * 3 / 4>(p, sm_count, st);
+  return launch_pairs_nv<Cfg, Cfg::N1>(p, sm_count, st);
 }
 
 cudaError_t launch_convolve(int L, const CUtensorMap* map, const ConvParams& p, int sm_count, cudaStream_t st) {

@@ -59,6 +59,22 @@ struct ListParams : BatchParams {
   const int64_t* unit_count = nullptr;
 };
 
+// Parameters of the pair-list kernel: one spectrum restricted to a list of (segment s, template
+// z) pairs, entries s*Z + z in ascending order, cut into equal contiguous ranges, one per warp.
+struct PairParams {
+  const float2* spec;       // n_bins complex64, 16-byte aligned
+  float* plane;             // Z x n_bins float32, row pitch n_bins
+  const float2* templates;  // Z x L template spectra (pair-major layout)
+  const float2* twist;      // L inter-pass twiddles (pair-major layout)
+  int* status;              // device status word (kStatusTimeout | kStatusBadList)
+  const int32_t* pairs;     // ascending entries s*Z + z
+  const int64_t* pair_count;  // list length in device memory (checked), or nullptr: n_pairs
+  int64_t n_pairs;          // entries, or the list's capacity with pair_count
+  int64_t n_bins;
+  int64_t nseg;             // ceil(n_bins / V)
+  int Z, V, h;
+};
+
 // Parameters of the forward-transform-only kernel (steps a2 + a3, for tests).
 struct SegParams {
   const float2* twist;
@@ -84,6 +100,11 @@ cudaError_t launch_batch(int L, const BatchParams& p, int sm_count, cudaStream_t
 // Single spectrum restricted to a work list of units g*Z + z (ascending).
 cudaError_t launch_units(int L, const ConvParams& p, const int32_t* units, const uint16_t* masks, int64_t n_units, int sm_count,
                          cudaStream_t stream, const int64_t* d_count = nullptr);
+
+// Whether segment length L has the pair-list kernel (one transform per warp: L = 2048).
+bool pairs_supported(int L);
+// Single spectrum restricted to a list of pairs s*Z + z (checked on the device first).
+cudaError_t launch_pairs(int L, const PairParams& p, int sm_count, cudaStream_t stream);
 
 // Launch helpers (defined in fdas_convolve.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_convolve(int L, const CUtensorMap* spec_map, const ConvParams& p, int sm_count,

@@ -128,12 +128,15 @@ extern "C" int fdas_static_check(fdas_stream_t stream) {
   DeviceScratch* sp = nullptr;
   int rc = device_scratch(&sp);
   if (rc != FDAS_OK) return rc;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int* status = reinterpret_cast<int*>(sp->base + kOffStatus);
   int word = 0;
-  if (cudaMemcpy(&word, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaMemcpyAsync(&word, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
   if (word == 0) return FDAS_OK;
-  if (cudaMemset(status, 0, sizeof(int)) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
   return (word & fdas::kStatusTimeout) ? FDAS_ERR_TIMEOUT : FDAS_ERR_INVALID;
 }
 

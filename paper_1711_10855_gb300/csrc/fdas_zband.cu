@@ -419,6 +419,38 @@ __global__ void group_flags_kernel(const float* logits, int n_win, int Z, float 
   if (threadIdx.x == 0) counts[g] = cnt;
 }
 
+// Proposal -> pair list: segment s (outputs [s*V, (s+1)*V), seg_bins = V) is proposed for
+// template z if a window whose central bins [w*hop, (w+1)*hop) meet [s*V - h, (s+1)*V + h) has
+// sigmoid(logit) >= threshold at a template within z_halo of z.  One block per segment: the
+// largest logit of each template over the segment's windows, then the dilation over +-z_halo
+// templates, in shared memory (Z floats).  mask[s][z] = 1 for a listed pair.
+__global__ void segment_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, int z_halo, int hop,
+                                     int64_t seg_bins, int h, uint16_t* masks, int* counts) {
+  extern __shared__ float smax[];
+  const int64_t s = blockIdx.x;
+  const int64_t lo = s * seg_bins - h, hi = (s + 1) * seg_bins + h;
+  const int w0 = (int)((lo > 0 ? lo : 0) / hop);
+  int w1 = (int)((hi + hop - 1) / hop);
+  if (w1 > n_win) w1 = n_win;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  for (int z = threadIdx.x; z < Z; z += blockDim.x) {
+    float m = -INFINITY;
+    for (int w = w0; w < w1; ++w) m = fmaxf(m, logits[(size_t)w * Z + z]);   // NaN logits never list
+    smax[z] = m;
+  }
+  __syncthreads();
+  for (int z = threadIdx.x; z < Z; z += blockDim.x) {
+    const int a = z - z_halo > 0 ? z - z_halo : 0, b = z + z_halo < Z - 1 ? z + z_halo : Z - 1;
+    bool f = false;
+    for (int q = a; q <= b && !f; ++q) f = smax[q] >= logit_thr;
+    masks[(size_t)s * Z + z] = f ? 1 : 0;
+    if (f) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) counts[s] = cnt;
+}
+
 // Exclusive scan of per-group counts and the total: one block of 1024 threads, thread t owning
 // the contiguous chunk [t c, (t+1) c) of the groups; chunk sums are scanned with warp shuffles.
 __global__ void __launch_bounds__(1024) scan_counts_kernel(const int* counts, int n_groups, int64_t* offsets,
@@ -843,6 +875,10 @@ struct fdas_zband {
   const void* cap_spec = nullptr;
   int64_t cap_n = 0;
   const void* cap_logits = nullptr;
+  // the synchronous host accessors run on `own`; `done` marks the last work enqueued on the net
+  // (they and fdas_zband_destroy wait for it, not for the whole device)
+  cudaStream_t own = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 namespace {
@@ -854,7 +890,28 @@ void free_zband(fdas_zband* z) {
   if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
   if (z->graph) cudaGraphDestroy(z->graph);
   if (z->capture_stream) cudaStreamDestroy(z->capture_stream);
+  if (z->own) cudaStreamDestroy(z->own);
+  if (z->done) cudaEventDestroy(z->done);
   delete z;
+}
+
+// Record the net's completion event after work enqueued on `st` (not while `st` is being captured
+// into a CUDA graph: a captured record is no event the host can wait on).
+int note_work(fdas_zband* z, cudaStream_t st, cudaError_t launch) {
+  if (launch != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return FDAS_OK;
+  return cudaEventRecord(z->done, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+// Host copy between the net's buffers and host memory on its own stream, after the net's last
+// enqueued work; returns when the copy has completed.
+int host_copy(fdas_zband* z, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  if (cudaStreamWaitEvent(z->own, z->done, 0) != cudaSuccess ||
+      cudaMemcpyAsync(dst, src, bytes, kind, z->own) != cudaSuccess || cudaStreamSynchronize(z->own) != cudaSuccess)
+    return FDAS_ERR_CUDA;
+  return FDAS_OK;
 }
 
 // Layers 1..3, pooling and head on B windows `in` (FP32 activations; FP32 or FP16 weights).
@@ -953,10 +1010,13 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
             cudaMalloc(&z->loss_part, (B * (size_t)n_out + 31) / 32 * 4) == cudaSuccess &&
             cudaMalloc(&z->wpart, B * (size_t)(window / kTile) * ((size_t)kC * kC * kK + kC) * 4) == cudaSuccess &&
             cudaMalloc(&z->sel, sizeof(SelectState)) == cudaSuccess &&
-            cudaMalloc(&z->scale, 4) == cudaSuccess && cudaMalloc(&z->status, 4) == cudaSuccess;
-  if (!ok || cudaMemset(z->p, 0, P * 4) != cudaSuccess || cudaMemset(z->ph, 0, P * 2) != cudaSuccess ||
-      cudaMemset(z->m, 0, P * 4) != cudaSuccess || cudaMemset(z->v, 0, P * 4) != cudaSuccess ||
-      cudaMemset(z->status, 0, 4) != cudaSuccess) {
+            cudaMalloc(&z->scale, 4) == cudaSuccess && cudaMalloc(&z->status, 4) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&z->own, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&z->done, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok || cudaMemsetAsync(z->p, 0, P * 4, z->own) != cudaSuccess ||
+      cudaMemsetAsync(z->ph, 0, P * 2, z->own) != cudaSuccess || cudaMemsetAsync(z->m, 0, P * 4, z->own) != cudaSuccess ||
+      cudaMemsetAsync(z->v, 0, P * 4, z->own) != cudaSuccess || cudaMemsetAsync(z->status, 0, 4, z->own) != cudaSuccess ||
+      cudaEventRecord(z->done, z->own) != cudaSuccess || cudaStreamSynchronize(z->own) != cudaSuccess) {
     cudaGetLastError();
     free_zband(z);
     return nullptr;
@@ -969,29 +1029,25 @@ int fdas_zband_param_count(const fdas_zband* z) { return z ? z->lay.total : FDAS
 int fdas_zband_set_params(fdas_zband* z, const float* host_params) {
   if (!z || !host_params) return FDAS_ERR_INVALID;
   const int P = z->lay.total;
-  if (cudaDeviceSynchronize() != cudaSuccess ||
-      cudaMemcpy(z->p, host_params, (size_t)P * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-    return FDAS_ERR_CUDA;
-  to_half_kernel<<<(P + 255) / 256, 256>>>(z->p, z->ph, P);
-  cudaMemset(z->m, 0, (size_t)P * 4);
-  cudaMemset(z->v, 0, (size_t)P * 4);
+  if (host_copy(z, z->p, host_params, (size_t)P * 4, cudaMemcpyHostToDevice) != FDAS_OK) return FDAS_ERR_CUDA;
+  to_half_kernel<<<(P + 255) / 256, 256, 0, z->own>>>(z->p, z->ph, P);
+  cudaMemsetAsync(z->m, 0, (size_t)P * 4, z->own);
+  cudaMemsetAsync(z->v, 0, (size_t)P * 4, z->own);
   z->step = 0;
-  return cudaDeviceSynchronize() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  if (note_work(z, z->own, cudaGetLastError()) != FDAS_OK) return FDAS_ERR_CUDA;
+  return cudaStreamSynchronize(z->own) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 int fdas_zband_get_params(fdas_zband* z, float* host_params) {
   if (!z || !host_params) return FDAS_ERR_INVALID;
-  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
-  return cudaMemcpy(host_params, z->p, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess
-             ? FDAS_OK
-             : FDAS_ERR_CUDA;
+  return host_copy(z, host_params, z->p, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost);
 }
 
 int fdas_zband_get_adam(fdas_zband* z, float* host_m, float* host_v, int* host_step) {
   if (!z || !host_m || !host_v || !host_step) return FDAS_ERR_INVALID;
   const size_t bytes = (size_t)z->lay.total * 4;
-  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(host_m, z->m, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(host_v, z->v, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (host_copy(z, host_m, z->m, bytes, cudaMemcpyDeviceToHost) != FDAS_OK ||
+      host_copy(z, host_v, z->v, bytes, cudaMemcpyDeviceToHost) != FDAS_OK)
     return FDAS_ERR_CUDA;
   *host_step = z->step;
   return FDAS_OK;
@@ -1000,8 +1056,8 @@ int fdas_zband_get_adam(fdas_zband* z, float* host_m, float* host_v, int* host_s
 int fdas_zband_set_adam(fdas_zband* z, const float* host_m, const float* host_v, int step) {
   if (!z || !host_m || !host_v || step < 0) return FDAS_ERR_INVALID;
   const size_t bytes = (size_t)z->lay.total * 4;
-  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(z->m, host_m, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(z->v, host_v, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+  if (host_copy(z, z->m, host_m, bytes, cudaMemcpyHostToDevice) != FDAS_OK ||
+      host_copy(z, z->v, host_v, bytes, cudaMemcpyHostToDevice) != FDAS_OK)
     return FDAS_ERR_CUDA;
   z->step = step;
   return FDAS_OK;
@@ -1042,7 +1098,7 @@ int fdas_zband_train_step(fdas_zband* z, const float* d_windows, const float* d_
   const float c1 = 1.f - powf(b1, (float)z->step), c2 = 1.f - powf(b2, (float)z->step);
   adam_kernel<<<(P + 255) / 256, 256, 0, st>>>(z->p, z->g, z->m, z->v, P, lr, b1, b2, 1e-8f, c1, c2);
   to_half_kernel<<<(P + 255) / 256, 256, 0, st>>>(z->p, z->ph, P);
-  if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;
+  if (note_work(z, st, cudaGetLastError()) != FDAS_OK) return FDAS_ERR_CUDA;
   if (host_loss) {
     if (cudaMemcpyAsync(host_loss, z->loss, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -1053,10 +1109,7 @@ int fdas_zband_train_step(fdas_zband* z, const float* d_windows, const float* d_
 
 int fdas_zband_gradients(fdas_zband* z, float* host_grads) {
   if (!z || !host_grads) return FDAS_ERR_INVALID;
-  if (cudaDeviceSynchronize() != cudaSuccess) return FDAS_ERR_CUDA;
-  return cudaMemcpy(host_grads, z->g, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess
-             ? FDAS_OK
-             : FDAS_ERR_CUDA;
+  return host_copy(z, host_grads, z->g, (size_t)z->lay.total * 4, cudaMemcpyDeviceToHost);
 }
 
 int fdas_zband_predict(fdas_zband* z, const float* d_windows, int batch, int half_weights, float* d_logits,
@@ -1070,7 +1123,7 @@ int fdas_zband_predict(fdas_zband* z, const float* d_windows, int batch, int hal
                         st) != cudaSuccess)
       return FDAS_ERR_CUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return note_work(z, st, cudaGetLastError());
 }
 
 // The launches of one proposal (median passes, then the fused inference) on `st`.
@@ -1147,16 +1200,19 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
     z->cap_n = n_bins;
     z->cap_logits = d_logits;
   }
-  return cudaGraphLaunch(z->graph_exec, st) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+  return note_work(z, st, cudaGraphLaunch(z->graph_exec, st));
 }
 
 int fdas_zband_check(fdas_zband* z, fdas_stream_t stream) {
   if (!z) return FDAS_ERR_INVALID;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FDAS_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int status = 0;
-  if (cudaMemcpy(&status, z->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return FDAS_ERR_CUDA;
+  if (cudaMemcpyAsync(&status, z->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FDAS_ERR_CUDA;
   if (status != 0) {
-    cudaMemset(z->status, 0, 4);
+    if (cudaMemsetAsync(z->status, 0, 4, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return FDAS_ERR_CUDA;
     return FDAS_ERR_TIMEOUT;
   }
   return FDAS_OK;
@@ -1240,9 +1296,34 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
                                       nullptr, d_scratch, host_count, stream);
 }
 
+int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, int z_halo, int hop,
+                          int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs, void* d_scratch,
+                          int64_t* host_count, fdas_stream_t stream) {
+  if (!d_logits || !d_pairs || !d_scratch || n_windows < 1 || n_windows > (1 << 30) || Z < 1 || Z > 8192 ||
+      !(threshold > 0.f && threshold < 1.f) || z_halo < 0 || z_halo > Z || hop < 1 || seg_bins < 1 || h < 0 ||
+      n_seg < 1 || n_seg > (1 << 24) || n_seg * (int64_t)Z > INT32_MAX || seg_bins > (int64_t(1) << 40))
+    return FDAS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(d_scratch) & 15u) return FDAS_ERR_ALIGN;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const float logit_thr = logf(threshold / (1.f - threshold));
+  unsigned char* scratch = static_cast<unsigned char*>(d_scratch);
+  int64_t* offsets = reinterpret_cast<int64_t*>(scratch);
+  int* counts = reinterpret_cast<int*>(scratch + align16(8 * (n_seg + 1)));
+  uint16_t* masks = reinterpret_cast<uint16_t*>(scratch + align16(8 * (n_seg + 1)) + align16(4 * n_seg));
+  segment_flags_kernel<<<(unsigned)n_seg, 256, sizeof(float) * (size_t)Z, st>>>(
+      d_logits, (int)n_windows, Z, logit_thr, z_halo, hop, seg_bins, h, masks, counts);
+  scan_counts_kernel<<<1, 1024, 0, st>>>(counts, (int)n_seg, offsets, offsets + n_seg);
+  write_units_kernel<<<(unsigned)n_seg, 256, 0, st>>>(masks, offsets, Z, d_pairs, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;
+  if (host_count && (cudaMemcpyAsync(host_count, offsets + n_seg, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess))
+    return FDAS_ERR_CUDA;
+  return FDAS_OK;
+}
+
 int fdas_zband_destroy(fdas_zband* z) {
   if (!z) return FDAS_OK;
-  cudaDeviceSynchronize();
+  if (z->done) cudaEventSynchronize(z->done);   // the net's last enqueued work, not the whole device
   free_zband(z);
   return FDAS_OK;
 }

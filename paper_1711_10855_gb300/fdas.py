@@ -37,7 +37,8 @@ EXPORTED = ["fdas_plan_create", "fdas_last_error", "fdas_error_string", "fdas_te
             "fdas_segment_spectra_tc", "fdas_zband_work_units_scratch_bytes",
             "fdas_convolve_power_units_masked", "fdas_zband_work_units_masked",
             "fdas_static_check", "fdas_static_selftest_wait_timeout",
-            "fdas_convolve_power_units_device_count"]
+            "fdas_convolve_power_units_device_count", "fdas_convolve_power_pairs",
+            "fdas_convolve_power_pairs_device_count", "fdas_zband_work_pairs"]
 
 _lock = threading.Lock()
 _lib = None
@@ -148,6 +149,12 @@ def lib() -> ctypes.CDLL:
             L.fdas_convolve_power_units_device_count.restype = i32
             L.fdas_static_check.argtypes = [vp]
             L.fdas_static_check.restype = i32
+            L.fdas_convolve_power_pairs.argtypes = [vp, vp, vp, vp, i64, vp]
+            L.fdas_convolve_power_pairs.restype = i32
+            L.fdas_convolve_power_pairs_device_count.argtypes = [vp, vp, vp, vp, vp, i64, vp]
+            L.fdas_convolve_power_pairs_device_count.restype = i32
+            L.fdas_zband_work_pairs.argtypes = [vp, i64, i32, f32, i32, i32, i64, i32, i64, vp, vp, vp, vp]
+            L.fdas_zband_work_pairs.restype = i32
             L.fdas_static_selftest_wait_timeout.argtypes = [i64, vp]
             L.fdas_static_selftest_wait_timeout.restype = i32
             _lib = L
@@ -270,6 +277,21 @@ class Plan:
                                                             ctypes.c_void_p(int(count_ptr)), int(max_units),
                                                             _stream(stream)),
                "fdas_convolve_power_units_device_count")
+
+    def convolve_power_pairs(self, spectrum, plane, pairs, n_pairs: int, stream=None):
+        """Only the listed (segment, template) pairs s*Z + z (ascending int32 device tensor) are
+        computed, spread evenly over the warps of the grid (seg_len 2048)."""
+        _check(lib().fdas_convolve_power_pairs(self._h, _ptr(spectrum), _ptr(plane), _ptr(pairs), int(n_pairs),
+                                               _stream(stream)), "fdas_convolve_power_pairs")
+
+    def convolve_power_pairs_device_count(self, spectrum, plane, pairs, count_ptr: int, max_pairs: int,
+                                          stream=None):
+        """As convolve_power_pairs with the list length read on the device at address count_ptr
+        (an int64, e.g. the one zband_work_pairs(..., host_count=False) leaves in its scratch)."""
+        _check(lib().fdas_convolve_power_pairs_device_count(self._h, _ptr(spectrum), _ptr(plane), _ptr(pairs),
+                                                            ctypes.c_void_p(int(count_ptr)), int(max_pairs),
+                                                            _stream(stream)),
+               "fdas_convolve_power_pairs_device_count")
 
     def template_taps(self, z_idx: int) -> np.ndarray:
         out = np.empty(2 * (self.tmpl_len + 1), dtype=np.float64)
@@ -435,6 +457,21 @@ def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: in
                                        None if scratch is None else _ptr(scratch), ctypes.byref(count),
                                        _stream(stream)), "fdas_zband_work_units")
     return count.value
+
+
+def zband_work_pairs(logits, n_windows: int, n_z: int, threshold: float, z_halo: int, hop: int, seg_bins: int,
+                     h: int, n_seg: int, pairs, scratch, stream=None, host_count: bool = True):
+    """Pair list s*Z + z into `pairs` (room for n_seg * n_z int32): a template is listed for a
+    segment when one within z_halo of it reaches `threshold` in a block the segment draws on.
+    `scratch`: zband_work_units_scratch_bytes(n_seg, n_z) bytes.  Returns the length
+    (synchronises the stream), or None with host_count=False (the length stays in the scratch,
+    zband_work_units_count_ptr(scratch, n_seg))."""
+    count = ctypes.c_int64(0)
+    _check(lib().fdas_zband_work_pairs(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(z_halo),
+                                       int(hop), int(seg_bins), int(h), int(n_seg), _ptr(pairs), _ptr(scratch),
+                                       ctypes.byref(count) if host_count else None, _stream(stream)),
+           "fdas_zband_work_pairs")
+    return count.value if host_count else None
 
 
 def zband_work_units_count_ptr(scratch, n_groups: int) -> int:

@@ -187,68 +187,92 @@ def train(net: "fdas.ZBand", data: TrainingSet, steps: int, batch: int = 256, lr
 
 
 class ProposalSearch:
-    """The proposal path for one plan: logits -> work list -> partial plane (async except the
-    work-list length, which the host needs to size the launch)."""
+    """The proposal path for one plan: logits -> work list -> partial plane.
 
-    def __init__(self, net: "fdas.ZBand", plan: "fdas.Plan", device=None, segment_masks: bool = True):
+    pairs=True (the default at seg_len 2048): the list holds (segment, template) pairs s*Z + z,
+    each proposal widened by z_halo templates on both sides, and the pair-list kernel spreads them
+    evenly over the grid's warps.  pairs=False: (segment group, template) units, with per-segment
+    masks when segment_masks is set."""
+
+    def __init__(self, net: "fdas.ZBand", plan: "fdas.Plan", device=None, segment_masks: bool = True,
+                 pairs: bool | None = None, z_halo: int = 0):
         import torch
         dev = device or torch.device("cuda")
         if net.window != WINDOW or net.n_out != plan.n_z:
             raise ValueError("net and plan do not match")
         self.net, self.plan = net, plan
+        self.pairs = plan.seg_len == 2048 if pairs is None else bool(pairs)
+        self.z_halo = int(z_halo)
         self.n_blocks = net.n_blocks(plan.n_bins)
         self.G = plan.group_segments
         self.n_groups = -(-plan.n_seg // self.G)
+        self.n_lists = plan.n_seg if self.pairs else self.n_groups   # list rows: segments or groups
         self.logits = torch.empty((self.n_blocks, plan.n_z), dtype=torch.float32, device=dev)
-        self.units = torch.empty(self.n_groups * plan.n_z, dtype=torch.int32, device=dev)
-        self.scratch = torch.empty(fdas.zband_work_units_scratch_bytes(self.n_groups, plan.n_z), dtype=torch.uint8,
+        self.units = torch.empty(self.n_lists * plan.n_z, dtype=torch.int32, device=dev)
+        self.scratch = torch.empty(fdas.zband_work_units_scratch_bytes(self.n_lists, plan.n_z), dtype=torch.uint8,
                                    device=dev)
         # segment bits of each listed unit (None: every segment of a listed unit's group is computed)
-        self.masks = torch.empty(self.n_groups * plan.n_z, dtype=torch.int16, device=dev) if segment_masks else None
+        self.masks = None
+        if segment_masks and not self.pairs:
+            self.masks = torch.empty(self.n_groups * plan.n_z, dtype=torch.int16, device=dev)
         self.n_units = 0
+
+    def _work_list(self, threshold: float, stream=None, host_count: bool = True):
+        plan = self.plan
+        if self.pairs:
+            return fdas.zband_work_pairs(self.logits, self.n_blocks, plan.n_z, threshold, self.z_halo, HOP, plan.valid,
+                                         plan.tmpl_len // 2, plan.n_seg, self.units, self.scratch, stream=stream,
+                                         host_count=host_count)
+        return fdas.zband_work_units(self.logits, self.n_blocks, plan.n_z, threshold, HOP, self.G * plan.valid,
+                                     plan.tmpl_len // 2, self.n_groups, self.units, stream=stream,
+                                     scratch=self.scratch, masks=self.masks,
+                                     segments=self.G if self.masks is not None else 1, host_count=host_count)
 
     def propose(self, spectrum, threshold: float) -> int:
         self.net.propose(spectrum, self.plan.n_bins, self.logits)
-        self.n_units = fdas.zband_work_units(self.logits, self.n_blocks, self.plan.n_z, threshold, HOP,
-                                             self.G * self.plan.valid, self.plan.tmpl_len // 2, self.n_groups,
-                                             self.units, scratch=self.scratch, masks=self.masks,
-                                             segments=self.G if self.masks is not None else 1)
+        self.n_units = self._work_list(threshold)
         return self.n_units
 
     def search(self, spectrum, plane, threshold: float) -> int:
         """Proposal plus the partial correlation into `plane` (cells outside the list untouched)."""
         n = self.propose(spectrum, threshold)
         if n > 0:
-            self.plan.convolve_power_units(spectrum, plane, self.units, n, masks=self.masks)
+            if self.pairs:
+                self.plan.convolve_power_pairs(spectrum, plane, self.units, n)
+            else:
+                self.plan.convolve_power_units(spectrum, plane, self.units, n, masks=self.masks)
         return n
 
     def search_async(self, spectrum, plane, threshold: float, stream=None) -> None:
         """As search, without any host synchronisation: the work list's length stays on the device
         and the correlation reads it there (read it afterwards with device_units())."""
         self.net.propose(spectrum, self.plan.n_bins, self.logits, stream)
-        fdas.zband_work_units(self.logits, self.n_blocks, self.plan.n_z, threshold, HOP, self.G * self.plan.valid,
-                              self.plan.tmpl_len // 2, self.n_groups, self.units, stream=stream, scratch=self.scratch,
-                              masks=self.masks, segments=self.G if self.masks is not None else 1, host_count=False)
-        self.plan.convolve_power_units_device_count(spectrum, plane, self.units,
-                                                    fdas.zband_work_units_count_ptr(self.scratch, self.n_groups),
-                                                    self.n_groups * self.plan.n_z, stream, masks=self.masks)
+        self._work_list(threshold, stream=stream, host_count=False)
+        count = fdas.zband_work_units_count_ptr(self.scratch, self.n_lists)
+        capacity = self.n_lists * self.plan.n_z
+        if self.pairs:
+            self.plan.convolve_power_pairs_device_count(spectrum, plane, self.units, count, capacity, stream)
+        else:
+            self.plan.convolve_power_units_device_count(spectrum, plane, self.units, count, capacity, stream,
+                                                        masks=self.masks)
         self.n_units = None
 
     def device_units(self) -> int:
         """Length of the last list made on the device (synchronises the current stream)."""
         import torch
-        cnt = self.scratch[8 * self.n_groups:8 * self.n_groups + 8].view(torch.int64)
+        cnt = self.scratch[8 * self.n_lists:8 * self.n_lists + 8].view(torch.int64)
         self.n_units = int(cnt.item())
         return self.n_units
 
     @property
     def unit_fraction(self) -> float:
-        return self.n_units / float(self.n_groups * self.plan.n_z)
+        """Fraction of the list's rows x templates listed (pairs, or segment-group units)."""
+        return self.n_units / float(self.n_lists * self.plan.n_z)
 
     @property
     def segment_fraction(self) -> float:
-        """Fraction of (segment, template) pairs the last list computes (its set mask bits)."""
-        if self.masks is None:
+        """Fraction of (segment, template) pairs the last list computes."""
+        if self.masks is None:   # pairs, or whole groups (every segment of a listed unit)
             return self.unit_fraction
         m = self.masks[:self.n_units].cpu().numpy().astype(np.uint16)
         bits = int(np.unpackbits(m.view(np.uint8)).sum())

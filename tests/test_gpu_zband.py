@@ -395,10 +395,12 @@ def test_masked_work_units_match_oracle(nw, Z, G, n_groups):
     np.testing.assert_array_equal(masks[:n].cpu().numpy().view(np.uint16), want_m)
 
 
-def test_device_count_path_matches_host_count_path():
+@pytest.mark.parametrize("pairs", [False, True])
+def test_device_count_path_matches_host_count_path(pairs):
     """A proposal's work list and its correlation without a host synchronisation (the list length
     read on the device) write exactly the cells the host-count path writes; a device count beyond
-    the list's capacity is rejected on the device and nothing runs."""
+    the list's capacity is rejected on the device and nothing runs.  Group units with segment
+    masks, and (segment, template) pairs with a z halo."""
     from paper_1711_10855_gb300 import zband as zb
     n_bins = 200_000
     spec = dev(synth.noise_spectrum(n_bins, 95))
@@ -406,7 +408,7 @@ def test_device_count_path_matches_host_count_path():
         plan.build_templates()
         vec, _ = make_params(21, 96)
         net.set_params(vec)
-        ps = zb.ProposalSearch(net, plan)
+        ps = zb.ProposalSearch(net, plan, pairs=pairs, z_halo=2 if pairs else 0)
         a = torch.full((plan.n_z, n_bins), float("nan"), dtype=torch.float32, device="cuda")
         b = torch.full_like(a, float("nan"))
         thr = 0.3
@@ -418,19 +420,24 @@ def test_device_count_path_matches_host_count_path():
         assert torch.equal(torch.isnan(a), torch.isnan(b))
         assert torch.equal(torch.nan_to_num(a, nan=-1.0), torch.nan_to_num(b, nan=-1.0))
         # a count above the capacity: the check kernel flags the list, the correlation does not run
-        bad = torch.tensor([ps.n_groups * plan.n_z + 1], dtype=torch.int64, device="cuda")
+        cap = ps.n_lists * plan.n_z
         c = torch.full_like(a, float("nan"))
-        plan.convolve_power_units_device_count(spec, c, ps.units, bad.data_ptr(), ps.n_groups * plan.n_z,
-                                               masks=ps.masks)
+
+        def run(count):
+            cnt = torch.tensor([count], dtype=torch.int64, device="cuda")
+            if pairs:
+                plan.convolve_power_pairs_device_count(spec, c, ps.units, cnt.data_ptr(), cap)
+            else:
+                plan.convolve_power_units_device_count(spec, c, ps.units, cnt.data_ptr(), cap, masks=ps.masks)
+
+        run(cap + 1)
         with pytest.raises(fdas.FdasError) as e:
             plan.check()
         assert e.value.code == fdas.FDAS_ERR_INVALID
         assert torch.isnan(c).all()
         # a negative count is rejected the same way; an empty list computes nothing and is valid
         for count, ok in ((-1, False), (0, True)):
-            cnt = torch.tensor([count], dtype=torch.int64, device="cuda")
-            plan.convolve_power_units_device_count(spec, c, ps.units, cnt.data_ptr(), ps.n_groups * plan.n_z,
-                                                   masks=ps.masks)
+            run(count)
             if ok:
                 plan.check()
             else:

@@ -190,6 +190,37 @@ def test_work_unit_masks_hand_case_and_group_flags():
     assert np.all(m2 == 1)
 
 
+def test_work_pairs_hand_computed():
+    """Pair lists on a hand-computed case, with and without the z halo."""
+    # blocks of hop 4; 3-bin segments, h = 1: segment s draws on [3s - 1, 3s + 4)
+    logits = np.full((4, 5), -10.0)
+    logits[1, 0] = 10.0          # block 1 = bins [4, 8): segments 1 ([2, 7)) and 2 ([5, 10))
+    logits[3, 4] = 10.0          # block 3 = bins [12, 16): segment 3 ([8, 13)) and 4 ([11, 16))
+    got = zband.work_pairs(logits, 0.5, 0, 4, 3, 1, 5)
+    np.testing.assert_array_equal(got, [1 * 5 + 0, 2 * 5 + 0, 3 * 5 + 4, 4 * 5 + 4])
+    # halo 1: templates 0..1 for segments 1, 2; 3..4 for segments 3, 4
+    got = zband.work_pairs(logits, 0.5, 1, 4, 3, 1, 5)
+    np.testing.assert_array_equal(got, [5, 6, 10, 11, 18, 19, 23, 24])
+    # halo >= Z - 1: every template of a proposed segment; segment 0 ([-1, 4): block 0) has none
+    got = zband.work_pairs(logits, 0.5, 5, 4, 3, 1, 5)
+    np.testing.assert_array_equal(got, np.arange(5, 25))
+
+
+def test_work_pairs_reduce_to_work_units_and_dilate():
+    """Halo 0 is the work list with one segment per group; a halo k lists exactly the templates
+    within k of a halo-0 pair of the same segment."""
+    rng = np.random.default_rng(9)
+    lg = rng.normal(-3.0, 2.0, (40, 23))
+    V, n_seg = 1536, 14
+    p0 = zband.work_pairs(lg, 0.3, 0, 512, V, 256, n_seg)
+    np.testing.assert_array_equal(p0, zband.work_units(lg, 0.3, 512, V, 256, n_seg))
+    Z = lg.shape[1]
+    for k in (1, 4):
+        base = {(int(u) // Z, int(u) % Z) for u in p0}
+        want = sorted({s * Z + z for (s, z0) in base for z in range(max(0, z0 - k), min(Z, z0 + k + 1))})
+        np.testing.assert_array_equal(zband.work_pairs(lg, 0.3, k, 512, V, 256, n_seg), want)
+
+
 # ---- running error bounds (the tolerances of the GPU tests of the network) -----------------
 
 def _bound_case(Z=21, W=512, B=6, seed=7):
