@@ -320,12 +320,16 @@ def run_zband(args):
     """The learned z-band proposal path on the survey plane, measured against the full search.
 
     The network is first trained, untimed, on windows whose labels the full search produces.  A
-    timed step is the whole proposal path through the library: fdas_zband_propose over the
-    spectrum (median selection + the fused tensor-core kernel), the work list
-    (fdas_zband_work_units, which reads its length back to the host), and
-    fdas_convolve_power_units over the listed units.  value = cells of the full plane / step
-    time (the plane the full search would compute); recall = the fraction of the full search's
-    detections (block maxima >= 20 x the noise power) the partial plane holds."""
+    timed step is the whole proposal path through the library, on the device without a host
+    synchronisation: fdas_zband_propose over the spectrum (median selection + the fused
+    tensor-core inference), the pair list (fdas_zband_work_pairs, its length left on the device)
+    and fdas_convolve_power_pairs_device_count over the listed (segment, template) pairs.
+    value = cells of the full plane / step time (the plane the full search would compute);
+    recall = the fraction of the full search's detections (block maxima >= 20 x the noise power)
+    the partial plane holds.  The operating point (threshold, z halo) is calibrated, untimed, on a
+    held-out spectrum (a chirp in every 16th block, SNR as in training, its own seed): the point of
+    the grid with the fewest pairs whose recall there reaches --zband-recall; the survey spectrum
+    and a dense spectrum of the same recipe (another seed) are then measured at that point."""
     import torch
     from paper_1711_10855_gb300 import build as fdas_build
     from paper_1711_10855_gb300 import fdas
@@ -350,7 +354,6 @@ def run_zband(args):
     part = torch.empty_like(full)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ps = zb.ProposalSearch(net, plan)
     cells = plan.n_z * w.n_bins
 
     def event_ms(fn, reps):
@@ -365,55 +368,65 @@ def run_zband(args):
             out.append(a.elapsed_time(b))
         return statistics.median(out)
 
+    def chirp_spectrum(seed):
+        rng = np.random.default_rng(seed)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        chirps = zb.chirp_blocks(rng, 1, w.n_bins, w.zmax, tuple(args.zband_snr), every=16,
+                                 snr_dist=args.zband_snr_dist)
+        return zb.chirp_spectra(torch, w.n_bins, chirps, gen, dev)[0], int(chirps["z"].shape[1])
+
     full_ms = event_ms(lambda: plan.convolve_power(spec, full), 5)
     plan.check()
-    propose_ms = event_ms(lambda: net.propose(spec, w.n_bins, ps.logits), 5)
+    searches = {k: zb.ProposalSearch(net, plan, pairs=True, z_halo=k) for k in args.zband_halos}
+    ps0 = searches[args.zband_halos[0]]
+    propose_ms = event_ms(lambda: net.propose(spec, w.n_bins, ps0.logits), 5)
     net.check()
-    points = []
-    for thr in args.zband_thresholds:
-        part.fill_(float("nan"))
-        n_units = ps.search(spec, part, thr)
+
+    def grid(s):
+        """Recall, pairs and step time (CUDA events, median of 5) at every grid point on spectrum s."""
+        plan.convolve_power(s, full)
         plan.check()
-        rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
-        point = {"threshold": thr, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
-                 "segment_fraction": ps.segment_fraction, "units": int(n_units)}
-        # the device-resident path at this threshold, CUDA events (L2 flushed before each run)
-        point["ms"] = event_ms(lambda: ps.search_async(spec, part, thr, stream), 10)
-        points.append(point)
-    # the same thresholds without segment masks (every segment of a listed unit's group computed)
-    ps_group = zb.ProposalSearch(net, plan, segment_masks=False)
-    group_points = []
-    for thr in args.zband_thresholds:
-        part.fill_(float("nan"))
-        n_units = ps_group.search(spec, part, thr)
-        plan.check()
-        rec, n_det, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
-        group_points.append({"threshold": thr, "recall": rec, "unit_fraction": ps_group.unit_fraction,
-                             "units": int(n_units),
-                             "ms": event_ms(lambda: ps_group.search_async(spec, part, thr, stream), 10)})
-    del ps_group
-    # a denser check of recall: 2^22 bins with a chirp in every 16th block (SNR as in training)
-    rng = np.random.default_rng(171110859)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(171110859)
-    chirps = zb.chirp_blocks(rng, 1, w.n_bins, w.zmax, tuple(args.zband_snr), every=16, snr_dist=args.zband_snr_dist)
-    spec2 = zb.chirp_spectra(torch, w.n_bins, chirps, gen, dev)[0]
-    plan.convolve_power(spec2, full)
+        out = []
+        for k, ps in searches.items():
+            for thr in args.zband_thresholds:
+                part.fill_(float("nan"))
+                n = ps.search(s, part, thr)
+                plan.check()
+                rec, n_det, _, _ = zb.recall(torch, full, part, s, w.n_bins)
+                point = {"z_halo": k, "threshold": thr, "recall": rec, "detections": n_det,
+                         "pair_fraction": ps.unit_fraction, "pairs": int(n)}
+                point["ms"] = event_ms(lambda: ps.search_async(s, part, thr, stream), 5)
+                out.append(point)
+        return out
+
+    calib, n_calib = chirp_spectrum(171110860)
+    calib_points = grid(calib)
+    del calib
+    reach = [p for p in calib_points if p["recall"] >= args.zband_recall]
+    chosen = (min(reach, key=lambda p: p["pair_fraction"]) if reach
+              else max(calib_points, key=lambda p: (p["recall"], -p["pair_fraction"])))
+    k, thr = chosen["z_halo"], chosen["threshold"]
+    dense, n_dense = chirp_spectrum(171110859)
+    dense_points = grid(dense)
+    del dense
+    survey_points = grid(spec)      # leaves the survey's full plane in `full`
+    at = lambda pts: next(p for p in pts if p["z_halo"] == k and p["threshold"] == thr)
+    # the group-unit path with segment masks at the same threshold, for comparison (no z halo)
+    ps_groups = zb.ProposalSearch(net, plan, pairs=False)
+    part.fill_(float("nan"))
+    n_units = ps_groups.search(spec, part, thr)
     plan.check()
-    dense_points = []
-    for t in args.zband_thresholds:
-        part.fill_(float("nan"))
-        n_units = ps.search(spec2, part, t)
-        plan.check()
-        rec, n_det, _, _ = zb.recall(torch, full, part, spec2, w.n_bins)
-        dense_points.append({"threshold": t, "recall": rec, "detections": n_det, "unit_fraction": ps.unit_fraction,
-                             "segment_fraction": ps.segment_fraction, "units": int(n_units)})
-    del spec2
-    thr = args.zband_thresholds[0]
+    g_rec, _, _, _ = zb.recall(torch, full, part, spec, w.n_bins)
+    groups_point = {"threshold": thr, "recall": g_rec, "unit_fraction": ps_groups.unit_fraction,
+                    "pair_fraction": ps_groups.segment_fraction, "units": int(n_units),
+                    "ms": event_ms(lambda: ps_groups.search_async(spec, part, thr, stream), 5)}
+    del ps_groups
+    ps = searches[k]
     for _ in range(args.warmup):
         ps.search(spec, part, thr)
     plan.check()
-    # timed step: the whole path on the device (proposal, work list, correlation with the list
+    # timed step: the whole path on the device (proposal, pair list, correlation with the list
     # length read on the device), CUDA events on the launching stream; the list length is read
     # back after the timed region
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -429,7 +442,7 @@ def run_zband(args):
             e1.record(stream)
         torch.cuda.synchronize(dev)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    timed_units = ps.device_units()
+    timed_pairs = ps.device_units()
     plan.check()
     net.check()
     ms = sum(step_ms) / len(step_ms)
@@ -437,32 +450,37 @@ def run_zband(args):
     hop = zb.WINDOW // 2
     macs = ps.n_blocks * hop * (9 * 32 + 2 * 9 * 32 * 32) + ps.n_blocks * plan.n_z * 32
     tflops = 2.0 * macs / (propose_ms * 1e-3) / 1e12
+    dense_at = at(dense_points)
     line = {
         "metric": "effective f-fdot cells/s of the learned z-band proposal path (full-plane cells / path time)",
         "value": cells / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32",
         "data": "synthetic (survey spectrum; training windows labelled by the full search)",
         "config": {"workload": w.name + "-zband", "n_bins": w.n_bins, "n_z": plan.n_z, "window": zb.WINDOW,
-                   "hop": hop, "threshold": thr, "train_windows": n_windows, "train_detected": n_detected,
-                   "train_snr": list(args.zband_snr), "train_snr_dist": args.zband_snr_dist,
-                   "train_steps": args.zband_steps, "train_s": train_s, "final_loss": losses[-1][1],
-                   "l2": "512 MiB buffer written between timed steps",
+                   "hop": hop, "threshold": thr, "z_halo": k, "train_windows": n_windows,
+                   "train_detected": n_detected, "train_snr": list(args.zband_snr),
+                   "train_snr_dist": args.zband_snr_dist, "train_steps": args.zband_steps, "train_s": train_s,
+                   "final_loss": losses[-1][1], "l2": "512 MiB buffer written between timed steps",
                    "timing": "CUDA events around the device-resident path (list length read on the device, "
-                             "read back after the timed region)", "timed_units": timed_units},
-        "recall": points[0]["recall"], "unit_fraction": points[0]["unit_fraction"],
-        "full_search_ms": full_ms, "full_search_cells_per_s": cells / (full_ms * 1e-3),
-        "propose_ms": propose_ms, "operating_points": points, "operating_points_without_segment_masks": group_points,
-        "dense_operating_points": {"spectrum": f"2^22 bins, {int(chirps["z"].shape[1])} chirps (one per 16 blocks), "
-                                               f"SNR {args.zband_snr[0]:g}-{args.zband_snr[1]:g} {args.zband_snr_dist}",
-                                   "points": dense_points},
+                             "read back after the timed region)", "timed_pairs": timed_pairs},
+        "recall": at(survey_points)["recall"], "pair_fraction": at(survey_points)["pair_fraction"],
+        "full_search_ms": full_ms, "full_search_cells_per_s": cells / (full_ms * 1e-3), "propose_ms": propose_ms,
+        "calibration": {"spectrum": f"2^22 bins, {n_calib} chirps (one per 16 blocks), held out (seed 171110860)",
+                        "target_recall": args.zband_recall, "chosen": chosen, "points": calib_points},
+        "dense": {"spectrum": f"2^22 bins, {n_dense} chirps (one per 16 blocks), SNR {args.zband_snr[0]:g}-"
+                              f"{args.zband_snr[1]:g} {args.zband_snr_dist}",
+                  "recall": dense_at["recall"], "pair_fraction": dense_at["pair_fraction"], "ms": dense_at["ms"],
+                  "speedup_vs_full": full_ms / dense_at["ms"], "points": dense_points},
+        "operating_points": survey_points,
+        "groups_with_segment_masks": groups_point,
         "roofline": {"bound": "tensor", "kernel": "propose_kernel (+ median selection in the timed call)",
                      "achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                      "frac": tflops / float(peaks["bf16_tflops"]),
                      "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
                      "flops_per_launch": 2.0 * macs, "traffic": zband_traffic()},
-        # per step: median (1 init + 4 x (histogram, pick)) and the fused inference (10), the work
-        # list (3), and the list check + correlation when the list is not empty (2)
-        "clocks": clk.summary(), "gpu_launches": args.steps * (13 + (2 if points[0]["units"] > 0 else 0)),
+        # per step: median (init, three histogram passes, finish) and the fused inference (6), the
+        # pair list (3), the list check and the pair correlation (2)
+        "clocks": clk.summary(), "gpu_launches": args.steps * 11,
     }
     print(json.dumps(line), flush=True)
     net.close()
@@ -806,7 +824,9 @@ def main():
     ap.add_argument("--zband-snr", type=float, nargs=2, default=[5.0, 30.0])
     ap.add_argument("--zband-snr-dist", choices=["uniform", "log-uniform"], default="uniform")
     ap.add_argument("--zband-steps", type=int, default=8000)
-    ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.2, 0.05, 0.1, 0.3, 0.5])
+    ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.05, 0.1, 0.15, 0.2, 0.3, 0.5])
+    ap.add_argument("--zband-halos", type=int, nargs="+", default=[0, 4, 8, 12])
+    ap.add_argument("--zband-recall", type=float, default=0.97)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -56,69 +56,138 @@ struct Layout {
 };
 
 constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)
-constexpr int kSelBlocks = 1024; // grid of the median passes
+constexpr int kSelBlocks = 2048; // grid cap of the median passes
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 // Exact lower median of |A_r|^2 (rank (n-1)/2) by radix selection on the FP32 bit patterns
-// (non-negative floats order as unsigned integers): four passes of 8 bits, most significant
-// first.  Each pass histograms the digit of the values whose higher bits equal the prefix
-// found so far; select_pick_kernel then fixes that digit.  scale = ln 2 / median.
+// (non-negative floats order as unsigned integers): three passes over the spectrum histogram the
+// top 12 bits, then the next 10 bits of the values matching the digit found so far, then the last
+// 10; after each pass one block finds the digit holding the rank (a block scan of the histogram).
+// scale = ln 2 / median.
+constexpr int kSelBins0 = 4096, kSelBins = 1024;
+constexpr int kSelPer = 8;   // complex values per thread and pass iteration (four 16-byte loads)
 struct SelectState {
-  unsigned prefix, mask;   // bits fixed so far and their mask
-  long long k;             // rank of the median among the values matching the prefix
-  unsigned hist[256];
+  long long k;                 // rank of the median among the values matching `prefix`
+  unsigned prefix, mask;       // bits fixed so far and their mask
+  unsigned hist0[kSelBins0];   // bits 31..20
+  unsigned hist1[kSelBins];    // bits 19..10 of the values matching digit 0
+  unsigned hist2[kSelBins];    // bits 9..0 of the values matching digits 0 and 1
 };
 
 __device__ __forceinline__ float power_of(const float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
-__global__ void __launch_bounds__(256) select_hist_kernel(const float2* spec, int64_t n, SelectState* st, int shift) {
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0u;
+// PASS 0: top 12 bits of every value; PASS 1, 2: the next 10 bits of the values whose higher
+// bits equal st->prefix.  Values are read in 16-byte pairs from the first 16-byte boundary (an
+// 8-byte aligned spectrum's first value is counted on its own); the tail element by element.
+template <int PASS>
+__global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, int64_t n, SelectState* st) {
+  constexpr int NB = PASS == 0 ? kSelBins0 : kSelBins;
+  constexpr int SHIFT = PASS == 0 ? 20 : (PASS == 1 ? 10 : 0);
+  __shared__ unsigned h[NB];
+  for (int i = threadIdx.x; i < NB; i += 256) h[i] = 0u;
+  const unsigned prefix = PASS == 0 ? 0u : st->prefix, mask = PASS == 0 ? 0u : st->mask;
   __syncthreads();
-  const unsigned prefix = st->prefix, mask = st->mask;
   const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
-    const int64_t r = base + threadIdx.x;
-    unsigned bucket = 256u;
-    if (r < n) {
-      const unsigned bits = __float_as_uint(power_of(__ldg(spec + r)));
-      if ((bits & mask) == prefix) bucket = (bits >> shift) & 255u;
+  auto count = [&](float2 a, bool valid) {
+    unsigned bucket = 0xFFFFFFFFu;
+    if (valid) {
+      const unsigned bits = __float_as_uint(power_of(a));
+      if ((bits & mask) == prefix) bucket = (bits >> SHIFT) & (unsigned)(NB - 1);
     }
     // one shared atomic per distinct bucket of the warp
     const unsigned peers = __match_any_sync(0xffffffffu, bucket);
-    if (bucket < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[bucket], (unsigned)__popc(peers));
+    if (bucket != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bucket], (unsigned)__popc(peers));
+  };
+  const int off = (reinterpret_cast<uintptr_t>(spec) & 15u) ? 1 : 0;
+  if (off && blockIdx.x == 0 && threadIdx.x < 32)
+    count(threadIdx.x == 0 ? __ldg(spec) : make_float2(0.f, 0.f), threadIdx.x == 0 && n > 0);
+  spec += off;
+  n -= off;
+  const int64_t step = (int64_t)gridDim.x * 256 * kSelPer;
+  for (int64_t base = (int64_t)blockIdx.x * 256 * kSelPer; base < n; base += step) {
+    // thread t reads the pairs (base + 2(t + 256 j), +1), j < kSelPer / 2: coalesced 16-byte loads
+    float4 v[kSelPer / 2];
+#pragma unroll
+    for (int j = 0; j < kSelPer / 2; ++j) {
+      const int64_t r = base + 2 * ((int64_t)threadIdx.x + 256 * j);
+      v[j] = r + 1 < n ? __ldg(reinterpret_cast<const float4*>(spec + r))
+                       : make_float4(r < n ? spec[r].x : 0.f, r < n ? spec[r].y : 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kSelPer / 2; ++j) {
+      const int64_t r = base + 2 * ((int64_t)threadIdx.x + 256 * j);
+      count(make_float2(v[j].x, v[j].y), r < n);
+      count(make_float2(v[j].z, v[j].w), r + 1 < n);
+    }
   }
   __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
+  unsigned* out = PASS == 0 ? st->hist0 : (PASS == 1 ? st->hist1 : st->hist2);
+  for (int i = threadIdx.x; i < NB; i += 256)
+    if (h[i]) atomicAdd(&out[i], h[i]);
 }
 
-__global__ void select_pick_kernel(SelectState* st, int shift, float* scale) {
-  if (threadIdx.x != 0) return;
-  long long k = st->k;
-  int d = 0;
-  for (; d < 255; ++d) {
-    if (k < (long long)st->hist[d]) break;
-    k -= st->hist[d];
+// One block of 256 threads: the digit of histogram PASS holding rank st->k (thread t owns the
+// bins [t*NB/256, (t+1)*NB/256); a block scan of their sums leaves exactly one thread whose range
+// holds the rank), appended to st->prefix; after the last digit, scale = ln 2 / median.
+template <int PASS>
+__global__ void __launch_bounds__(256) select_digit_kernel(SelectState* st, float* scale) {
+  constexpr int NB = PASS == 0 ? kSelBins0 : kSelBins;
+  constexpr int SHIFT = PASS == 0 ? 20 : (PASS == 1 ? 10 : 0);
+  constexpr int per = NB / 256;
+  __shared__ long long wsum[8];
+  const unsigned* hist = PASS == 0 ? st->hist0 : (PASS == 1 ? st->hist1 : st->hist2);
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  unsigned c[per];
+  long long own = 0;
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    c[i] = hist[t * per + i];
+    own += c[i];
   }
-  st->prefix |= (unsigned)d << shift;
-  st->mask |= 255u << shift;
-  st->k = k;
-  for (int i = 0; i < 256; ++i) st->hist[i] = 0u;
-  if (shift == 0) {
-    const float med = __uint_as_float(st->prefix);
-    *scale = med > 0.f ? 0.69314718055994531f / med : 0.f;
+  long long inc = own;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += y;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  long long excl = inc - own;
+  for (int i = 0; i < wid; ++i) excl += wsum[i];
+  const long long k = st->k;
+  if (k >= excl && k < excl + own) {
+    long long r = k - excl;
+    int d = t * per;
+#pragma unroll
+    for (int i = 0; i < per - 1; ++i)
+      if (d == t * per + i && r >= (long long)c[i]) {
+        r -= c[i];
+        ++d;
+      }
+    const unsigned prefix = (PASS == 0 ? 0u : st->prefix) | ((unsigned)d << SHIFT);
+    st->k = r;
+    st->prefix = prefix;
+    st->mask = PASS == 0 ? 0xFFF00000u : (PASS == 1 ? 0xFFFFFC00u : 0xFFFFFFFFu);
+    if (PASS == 2) {
+      const float med = __uint_as_float(prefix);
+      *scale = med > 0.f ? 0.69314718055994531f / med : 0.f;
+    }
   }
 }
 
-__global__ void select_init_kernel(SelectState* st, int64_t n) {
+__global__ void __launch_bounds__(256) select_init_kernel(SelectState* st, int64_t n) {
   if (threadIdx.x == 0) {
+    st->k = (n - 1) / 2;
     st->prefix = 0u;
     st->mask = 0u;
-    st->k = (n - 1) / 2;
   }
-  st->hist[threadIdx.x] = 0u;
+  for (int i = threadIdx.x; i < kSelBins0; i += 256) st->hist0[i] = 0u;
+  for (int i = threadIdx.x; i < kSelBins; i += 256) {
+    st->hist1[i] = 0u;
+    st->hist2[i] = 0u;
+  }
 }
 
 __device__ __forceinline__ float power_x(const float2* spec, int64_t n, int64_t r, float scale) {
@@ -940,15 +1009,17 @@ cudaError_t forward(fdas_zband* z, const float* in, int B, bool half_weights, cu
   return cudaGetLastError();
 }
 
-// scale = ln 2 / median |A|^2 into `scale`.
+// scale = ln 2 / median |A|^2 into `scale`: seven launches.
 void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* scale, cudaStream_t st) {
   select_init_kernel<<<1, 256, 0, st>>>(sel, n);
-  const int64_t blocks = (n + 255) / 256;
+  const int64_t blocks = (n + 256 * kSelPer - 1) / (256 * kSelPer);
   const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    select_hist_kernel<<<grid, 256, 0, st>>>(spec, n, sel, shift);
-    select_pick_kernel<<<1, 32, 0, st>>>(sel, shift, scale);
-  }
+  select_pass_kernel<0><<<grid, 256, 0, st>>>(spec, n, sel);
+  select_digit_kernel<0><<<1, 256, 0, st>>>(sel, scale);
+  select_pass_kernel<1><<<grid, 256, 0, st>>>(spec, n, sel);
+  select_digit_kernel<1><<<1, 256, 0, st>>>(sel, scale);
+  select_pass_kernel<2><<<grid, 256, 0, st>>>(spec, n, sel);
+  select_digit_kernel<2><<<1, 256, 0, st>>>(sel, scale);
 }
 }  // namespace
 
@@ -1168,7 +1239,7 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
   if ((reinterpret_cast<uintptr_t>(d_spectrum) & 7u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u))
     return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // ten launches replayed as one graph: captured again when the spectrum, its length or the
+  // eight launches replayed as one graph: captured again when the spectrum, its length or the
   // logits buffer change (the weights are read through fixed pointers, so training needs none)
   if (!(z->graph_exec && z->cap_spec == d_spectrum && z->cap_n == n_bins && z->cap_logits == d_logits)) {
     if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);

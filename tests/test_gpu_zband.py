@@ -165,6 +165,29 @@ def test_propose_matches_oracle_block_logits(W, n_bins):
     assert np.all(np.abs(got - want) <= bound), float(np.max(np.abs(got - want) / bound))
 
 
+@pytest.mark.parametrize("n_bins", [40000, 40001])
+def test_propose_on_8_byte_aligned_spectrum(n_bins):
+    """A spectrum view starting 8 bytes past a 16-byte boundary, even and odd lengths: the same
+    logits, bit for bit, as the aligned copy (the median passes read 16-byte pairs from the first
+    boundary and the first value on its own)."""
+    Z = 21
+    vec, _ = make_params(Z, 33)
+    spec = dev(chirp_spectrum(n_bins, 34, n_chirps=6, amp=0.2))
+    buf = torch.zeros(n_bins + 1, dtype=spec.dtype, device="cuda")
+    buf[1:] = spec
+    view = buf[1:]
+    assert view.data_ptr() % 16 == 8
+    with fdas.ZBand(1024, Z, 4) as net:
+        net.set_params(vec)
+        nb = net.n_blocks(n_bins)
+        a = torch.full((nb, Z), float("nan"), dtype=torch.float32, device="cuda")
+        b = torch.full_like(a, float("nan"))
+        net.propose(spec, n_bins, a)
+        net.propose(view, n_bins, b)
+        net.check()
+    assert not torch.isnan(a).any() and torch.equal(a, b)
+
+
 def test_propose_large_spectrum_sampled_blocks_and_predict_agreement():
     """2^20 bins (2048 blocks over the persistent grid): sampled blocks against the oracle, and
     every block against the windowed CUDA-core path (same FP16 weights)."""
