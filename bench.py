@@ -480,9 +480,9 @@ def run_zband(args):
                      "frac": tflops / float(peaks["bf16_tflops"]),
                      "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
                      "flops_per_launch": 2.0 * macs, "traffic": zband_traffic()},
-        # per step: median (init, three histogram passes, finish) and the fused inference (6), the
-        # pair list (3), the list check and the pair correlation (2)
-        "clocks": clk.summary(), "gpu_launches": args.steps * 11,
+        # per step: median (init, three histogram passes, three digit kernels) and the fused
+        # inference (8), the pair list (3), the list check and the pair correlation (2)
+        "clocks": clk.summary(), "gpu_launches": args.steps * 13,
     }
     print(json.dumps(line), flush=True)
     net.close()
