@@ -401,8 +401,9 @@ int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z
  * Writes the ascending list to d_pairs (room for n_seg*Z int32; n_seg*Z <= 2^31 - 1, Z <= 8192)
  * and its length to *host_count (synchronises `stream`), or with host_count NULL leaves it on
  * the device as the int64 at ((const int64_t*)d_scratch)[n_seg].  d_scratch: 16-byte aligned
- * caller workspace of fdas_zband_work_units_scratch_bytes(n_seg, Z) bytes (required).
- * Asynchronous when host_count is NULL; three launches, no allocation. */
+ * caller workspace of fdas_zband_work_units_scratch_bytes(n_seg, Z) bytes (required); d_logits
+ * and d_pairs 4-byte aligned (FDAS_ERR_ALIGN otherwise).  Asynchronous when host_count is NULL;
+ * three launches, no allocation. */
 int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, int z_halo, int hop,
                           int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs, void* d_scratch,
                           int64_t* host_count, fdas_stream_t stream);

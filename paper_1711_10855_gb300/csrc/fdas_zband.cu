@@ -1374,7 +1374,9 @@ int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float
       !(threshold > 0.f && threshold < 1.f) || z_halo < 0 || z_halo > Z || hop < 1 || seg_bins < 1 || h < 0 ||
       n_seg < 1 || n_seg > (1 << 24) || n_seg * (int64_t)Z > INT32_MAX || seg_bins > (int64_t(1) << 40))
     return FDAS_ERR_INVALID;
-  if (reinterpret_cast<uintptr_t>(d_scratch) & 15u) return FDAS_ERR_ALIGN;
+  if ((reinterpret_cast<uintptr_t>(d_scratch) & 15u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u) ||
+      (reinterpret_cast<uintptr_t>(d_pairs) & 3u))
+    return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float logit_thr = logf(threshold / (1.f - threshold));
   unsigned char* scratch = static_cast<unsigned char*>(d_scratch);

@@ -60,6 +60,10 @@ def test_work_pairs_rejects_bad_arguments():
         with pytest.raises(fdas.FdasError) as e:
             fdas.zband_work_pairs(logits, 4, 5, thr, halo, 512, 1536, 256, 4, pairs, scratch)
         assert e.value.code == fdas.FDAS_ERR_INVALID
+    raw = torch.empty(84, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fdas.FdasError) as e:   # a pair list 2 bytes off a 4-byte boundary
+        fdas.zband_work_pairs(logits, 4, 5, 0.5, 0, 512, 1536, 256, 4, raw[2:], scratch)
+    assert e.value.code == fdas.FDAS_ERR_ALIGN
 
 
 def _mask_of(pairs, Z, n_bins, V):
