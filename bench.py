@@ -452,6 +452,8 @@ def run_zband(args):
     hop = zb.WINDOW // 2
     macs = ps.n_blocks * hop * (9 * 32 + 2 * 9 * 32 * 32) + ps.n_blocks * plan.n_z * 32
     tflops = 2.0 * macs / (propose_ms * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    shape_tflops = 2.0 * 128 * 32 * 16 / 64 * sms * 2.07e9 / 1e12   # at the maximum SM clock
     dense_at = at(dense_points)
     line = {
         "metric": "effective f-fdot cells/s of the learned z-band proposal path (full-plane cells / path time)",
@@ -479,7 +481,11 @@ def run_zband(args):
                      "achieved": tflops, "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
                      "frac": tflops / float(peaks["bf16_tflops"]),
                      "peak_source": f"bf16_tflops burst ({peak_src}); FP16 dense rate equals BF16",
-                     "flops_per_launch": 2.0 * macs, "traffic": zband_traffic()},
+                     "flops_per_launch": 2.0 * macs, "traffic": zband_traffic(),
+                     # the layers' MMAs are M = 128, N = 32, K = 16: one occupies the tensor pipe ~64
+                     # cycles (a per-instruction floor below N = 128), a quarter of the dense rate
+                     "shape_peak": {"cycles_per_mma": 64, "tflops": shape_tflops,
+                                    "frac": tflops / shape_tflops}},
         # per step: median (init, three histogram passes, three digit kernels) and the fused
         # inference (8), the pair list (3), the list check and the pair correlation (2)
         "clocks": clk.summary(), "gpu_launches": args.steps * 13,
