@@ -378,7 +378,8 @@ def run_zband(args):
 
     full_ms = event_ms(lambda: plan.convolve_power(spec, full), 5)
     plan.check()
-    searches = {k: zb.ProposalSearch(net, plan, pairs=True, z_halo=k) for k in args.zband_halos}
+    searches = {k: zb.ProposalSearch(net, plan, pairs=True, z_halo=k, reach_threshold=args.zband_reach)
+                for k in args.zband_halos}
     ps0 = searches[args.zband_halos[0]]
     propose_ms = event_ms(lambda: net.propose(spec, w.n_bins, ps0.logits), 5)
     net.check()
@@ -403,8 +404,8 @@ def run_zband(args):
     calib, n_calib = chirp_spectrum(171110860)
     calib_points = grid(calib)
     del calib
-    reach = [p for p in calib_points if p["recall"] >= args.zband_recall]
-    chosen = (min(reach, key=lambda p: p["pair_fraction"]) if reach
+    hits = [p for p in calib_points if p["recall"] >= args.zband_recall]
+    chosen = (min(hits, key=lambda p: p["pair_fraction"]) if hits
               else max(calib_points, key=lambda p: (p["recall"], -p["pair_fraction"])))
     k, thr = chosen["z_halo"], chosen["threshold"]
     dense, n_dense = chirp_spectrum(171110859)
@@ -461,7 +462,8 @@ def run_zband(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32",
         "data": "synthetic (survey spectrum; training windows labelled by the full search)",
         "config": {"workload": w.name + "-zband", "n_bins": w.n_bins, "n_z": plan.n_z, "window": zb.WINDOW,
-                   "hop": hop, "threshold": thr, "z_halo": k, "train_windows": n_windows,
+                   "hop": hop, "threshold": thr, "z_halo": k, "reach_threshold": args.zband_reach,
+                   "train_windows": n_windows,
                    "train_detected": n_detected, "train_snr": list(args.zband_snr),
                    "train_snr_dist": args.zband_snr_dist, "train_steps": args.zband_steps, "train_s": train_s,
                    "final_loss": losses[-1][1], "l2": "512 MiB buffer written between timed steps",
@@ -835,6 +837,7 @@ def main():
     ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.05, 0.1, 0.15, 0.2, 0.3, 0.5])
     ap.add_argument("--zband-halos", type=int, nargs="+", default=[0, 4, 8, 12])
     ap.add_argument("--zband-recall", type=float, default=0.97)
+    ap.add_argument("--zband-reach", type=float, default=0.5)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

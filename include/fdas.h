@@ -393,20 +393,24 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
 int fdas_zband_work_units_masked(const float* d_logits, int64_t n_windows, int Z, float threshold, int hop,
                                  int64_t seg_bins, int G, int h, int64_t n_groups, int32_t* d_units,
                                  uint16_t* d_masks, void* d_scratch, int64_t* host_count, fdas_stream_t stream);
-/* Pair list from block logits (device, n_windows x Z), for fdas_convolve_power_pairs: pair
- * s*Z + z is listed when some template z' with |z' - z| <= z_halo (0 <= z_halo <= Z) has
- * sigmoid(logit) >= threshold (0 < threshold < 1) in a block w whose bins [w*hop, (w+1)*hop)
- * meet [s*seg_bins - h, (s+1)*seg_bins + h) (seg_bins = V).  z_halo widens each proposal by
- * z_halo templates on both sides, for signals whose template the network places only roughly.
- * Writes the ascending list to d_pairs (room for n_seg*Z int32; n_seg*Z <= 2^31 - 1, Z <= 8192)
- * and its length to *host_count (synchronises `stream`), or with host_count NULL leaves it on
- * the device as the int64 at ((const int64_t*)d_scratch)[n_seg].  d_scratch: 16-byte aligned
- * caller workspace of fdas_zband_work_units_scratch_bytes(n_seg, Z) bytes (required); d_logits
- * and d_pairs 4-byte aligned (FDAS_ERR_ALIGN otherwise).  Asynchronous when host_count is NULL;
- * three launches, no allocation. */
-int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, int z_halo, int hop,
-                          int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs, void* d_scratch,
-                          int64_t* host_count, fdas_stream_t stream);
+/* Pair list from block logits (device, n_windows x Z), for fdas_convolve_power_pairs.  Segment s
+ * (seg_bins = V) has the outputs [s*V, (s+1)*V) and draws on the inputs [s*V - h, (s+1)*V + h).
+ * A template q is proposed for it by a block w (bins [w*hop, (w+1)*hop)) that meets its outputs
+ * with sigmoid(logit[w][q]) >= threshold, or by a block that meets only the inputs beyond them
+ * with sigmoid(logit[w][q]) >= reach_threshold (only a strong signal there has a response that
+ * reaches the segment's outputs); pair s*Z + z is listed when a template within z_halo
+ * (0 <= z_halo <= Z) of z is proposed.  0 < threshold < 1, threshold <= reach_threshold <= 1
+ * (reach_threshold = threshold: every block the inputs meet counts alike).  z_halo widens each
+ * proposal for signals the network places only roughly in z.  Writes the ascending list to
+ * d_pairs (room for n_seg*Z int32; n_seg*Z <= 2^31 - 1, Z <= 8192) and its length to *host_count
+ * (synchronises `stream`), or with host_count NULL leaves it on the device as the int64 at
+ * ((const int64_t*)d_scratch)[n_seg].  d_scratch: 16-byte aligned caller workspace of
+ * fdas_zband_work_units_scratch_bytes(n_seg, Z) bytes (required); d_logits and d_pairs 4-byte
+ * aligned (FDAS_ERR_ALIGN otherwise).  Asynchronous when host_count is NULL; three launches, no
+ * allocation. */
+int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, float reach_threshold,
+                          int z_halo, int hop, int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs,
+                          void* d_scratch, int64_t* host_count, fdas_stream_t stream);
 /* Waits for the net's last enqueued work (not the whole device), then frees it. */
 int fdas_zband_destroy(fdas_zband* net);
 

@@ -206,20 +206,27 @@ def work_unit_masks(logits: np.ndarray, threshold: float, hop: int, seg_bins: in
 
 
 def work_pairs(logits: np.ndarray, threshold: float, z_halo: int, hop: int, seg_bins: int, h: int,
-               n_seg: int) -> np.ndarray:
-    """Ascending pairs s*Z + z: segment s (outputs [s*V, (s+1)*V), V = seg_bins, input bins
-    reaching h further on each side) is listed for template z when a block w whose bins
-    [w*hop, (w+1)*hop) meet [s*V - h, (s+1)*V + h) has sigmoid(logit[w, z']) >= threshold for
-    some template z' with |z' - z| <= z_halo."""
+               n_seg: int, reach_threshold: float | None = None) -> np.ndarray:
+    """Ascending pairs s*Z + z.  Segment s has the outputs [s*V, (s+1)*V) (V = seg_bins) and draws
+    on the inputs [s*V - h, (s+1)*V + h).  Template q is proposed for it by a block w (bins
+    [w*hop, (w+1)*hop)) meeting the outputs with sigmoid(logit[w, q]) >= threshold, or by a block
+    meeting only the inputs beyond them with sigmoid(logit[w, q]) >= reach_threshold (default:
+    threshold); (s, z) is listed when some proposed q has |q - z| <= z_halo."""
     nw, Z = logits.shape
-    keep = 1.0 / (1.0 + np.exp(-np.asarray(logits, dtype=np.float64))) >= threshold
+    prob = 1.0 / (1.0 + np.exp(-np.asarray(logits, dtype=np.float64)))
+    reach_threshold = threshold if reach_threshold is None else reach_threshold
     pairs = []
     for s in range(n_seg):
-        lo, hi = s * seg_bins - h, (s + 1) * seg_bins + h
-        blocks = [w for w in range(nw) if w * hop < hi and (w + 1) * hop > lo]
+        o0, o1 = s * seg_bins, (s + 1) * seg_bins
+        proposed = np.zeros(Z, dtype=bool)
+        for w in range(nw):
+            b0, b1 = w * hop, (w + 1) * hop
+            if b0 < o1 and b1 > o0:
+                proposed |= prob[w] >= threshold
+            elif b0 < o1 + h and b1 > o0 - h:
+                proposed |= prob[w] >= reach_threshold
         for z in range(Z):
-            near = range(max(0, z - z_halo), min(Z, z + z_halo + 1))
-            if any(keep[w, q] for w in blocks for q in near):
+            if proposed[max(0, z - z_halo):min(Z, z + z_halo + 1)].any():
                 pairs.append(s * Z + z)
     return np.asarray(pairs, dtype=np.int64)
 

@@ -488,31 +488,38 @@ __global__ void group_flags_kernel(const float* logits, int n_win, int Z, float 
   if (threadIdx.x == 0) counts[g] = cnt;
 }
 
-// Proposal -> pair list: segment s (outputs [s*V, (s+1)*V), seg_bins = V) is proposed for
-// template z if a window whose central bins [w*hop, (w+1)*hop) meet [s*V - h, (s+1)*V + h) has
-// sigmoid(logit) >= threshold at a template within z_halo of z.  One block per segment: the
-// largest logit of each template over the segment's windows, then the dilation over +-z_halo
-// templates, in shared memory (Z floats).  mask[s][z] = 1 for a listed pair.
-__global__ void segment_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, int z_halo, int hop,
-                                     int64_t seg_bins, int h, uint16_t* masks, int* counts) {
-  extern __shared__ float smax[];
+// Proposal -> pair list.  Segment s has the outputs [s*V, (s+1)*V) (seg_bins = V) and draws on
+// the inputs [s*V - h, (s+1)*V + h).  A template q is proposed for it by a block w (central bins
+// [w*hop, (w+1)*hop)) that meets its outputs with sigmoid(logit) >= threshold, or by a block that
+// meets only the inputs beyond them with sigmoid(logit) >= reach_threshold (a signal there must be
+// strong for its response to reach the segment's outputs); pair (s, z) is listed when a template
+// within z_halo of z is proposed.  One block per segment: the two maxima per template, the
+// proposed flags in shared memory (Z ints), then the dilation.  mask[s][z] = 1 for a listed pair.
+__global__ void segment_flags_kernel(const float* logits, int n_win, int Z, float logit_thr, float logit_reach,
+                                     int z_halo, int hop, int64_t seg_bins, int h, uint16_t* masks, int* counts) {
+  extern __shared__ int sflag[];
   const int64_t s = blockIdx.x;
-  const int64_t lo = s * seg_bins - h, hi = (s + 1) * seg_bins + h;
-  const int w0 = (int)((lo > 0 ? lo : 0) / hop);
-  int w1 = (int)((hi + hop - 1) / hop);
-  if (w1 > n_win) w1 = n_win;
+  const int64_t o0 = s * seg_bins, o1 = (s + 1) * seg_bins;   // outputs
+  const int64_t r0 = o0 - h, r1 = o1 + h;                     // inputs
+  auto clampw = [&](int64_t w) { return (int)(w < 0 ? 0 : (w > n_win ? n_win : w)); };
+  const int wr0 = clampw((r0 > 0 ? r0 : 0) / hop), wr1 = clampw((r1 + hop - 1) / hop);
+  const int wo0 = clampw(o0 / hop), wo1 = clampw((o1 + hop - 1) / hop);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   for (int z = threadIdx.x; z < Z; z += blockDim.x) {
-    float m = -INFINITY;
-    for (int w = w0; w < w1; ++w) m = fmaxf(m, logits[(size_t)w * Z + z]);   // NaN logits never list
-    smax[z] = m;
+    float own = -INFINITY, reach = -INFINITY;   // NaN logits never list
+    for (int w = wr0; w < wr1; ++w) {
+      const float v = logits[(size_t)w * Z + z];
+      if (w >= wo0 && w < wo1) own = fmaxf(own, v);
+      else reach = fmaxf(reach, v);
+    }
+    sflag[z] = (own >= logit_thr || reach >= logit_reach) ? 1 : 0;
   }
   __syncthreads();
   for (int z = threadIdx.x; z < Z; z += blockDim.x) {
     const int a = z - z_halo > 0 ? z - z_halo : 0, b = z + z_halo < Z - 1 ? z + z_halo : Z - 1;
     bool f = false;
-    for (int q = a; q <= b && !f; ++q) f = smax[q] >= logit_thr;
+    for (int q = a; q <= b && !f; ++q) f = sflag[q] != 0;
     masks[(size_t)s * Z + z] = f ? 1 : 0;
     if (f) atomicAdd(&cnt, 1);
   }
@@ -1367,11 +1374,12 @@ int fdas_zband_work_units(const float* d_logits, int64_t n_windows, int Z, float
                                       nullptr, d_scratch, host_count, stream);
 }
 
-int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, int z_halo, int hop,
-                          int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs, void* d_scratch,
-                          int64_t* host_count, fdas_stream_t stream) {
+int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float threshold, float reach_threshold,
+                          int z_halo, int hop, int64_t seg_bins, int h, int64_t n_seg, int32_t* d_pairs,
+                          void* d_scratch, int64_t* host_count, fdas_stream_t stream) {
   if (!d_logits || !d_pairs || !d_scratch || n_windows < 1 || n_windows > (1 << 30) || Z < 1 || Z > 8192 ||
-      !(threshold > 0.f && threshold < 1.f) || z_halo < 0 || z_halo > Z || hop < 1 || seg_bins < 1 || h < 0 ||
+      !(threshold > 0.f && threshold < 1.f) || !(reach_threshold >= threshold && reach_threshold <= 1.f) ||
+      z_halo < 0 || z_halo > Z || hop < 1 || seg_bins < 1 || h < 0 ||
       n_seg < 1 || n_seg > (1 << 24) || n_seg * (int64_t)Z > INT32_MAX || seg_bins > (int64_t(1) << 40))
     return FDAS_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(d_scratch) & 15u) || (reinterpret_cast<uintptr_t>(d_logits) & 3u) ||
@@ -1379,12 +1387,13 @@ int fdas_zband_work_pairs(const float* d_logits, int64_t n_windows, int Z, float
     return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float logit_thr = logf(threshold / (1.f - threshold));
+  const float logit_reach = reach_threshold < 1.f ? logf(reach_threshold / (1.f - reach_threshold)) : INFINITY;
   unsigned char* scratch = static_cast<unsigned char*>(d_scratch);
   int64_t* offsets = reinterpret_cast<int64_t*>(scratch);
   int* counts = reinterpret_cast<int*>(scratch + align16(8 * (n_seg + 1)));
   uint16_t* masks = reinterpret_cast<uint16_t*>(scratch + align16(8 * (n_seg + 1)) + align16(4 * n_seg));
-  segment_flags_kernel<<<(unsigned)n_seg, 256, sizeof(float) * (size_t)Z, st>>>(
-      d_logits, (int)n_windows, Z, logit_thr, z_halo, hop, seg_bins, h, masks, counts);
+  segment_flags_kernel<<<(unsigned)n_seg, 256, sizeof(int) * (size_t)Z, st>>>(
+      d_logits, (int)n_windows, Z, logit_thr, logit_reach, z_halo, hop, seg_bins, h, masks, counts);
   scan_counts_kernel<<<1, 1024, 0, st>>>(counts, (int)n_seg, offsets, offsets + n_seg);
   write_units_kernel<<<(unsigned)n_seg, 256, 0, st>>>(masks, offsets, Z, d_pairs, nullptr);
   if (cudaGetLastError() != cudaSuccess) return FDAS_ERR_CUDA;

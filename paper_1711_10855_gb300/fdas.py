@@ -153,7 +153,7 @@ def lib() -> ctypes.CDLL:
             L.fdas_convolve_power_pairs.restype = i32
             L.fdas_convolve_power_pairs_device_count.argtypes = [vp, vp, vp, vp, vp, i64, vp]
             L.fdas_convolve_power_pairs_device_count.restype = i32
-            L.fdas_zband_work_pairs.argtypes = [vp, i64, i32, f32, i32, i32, i64, i32, i64, vp, vp, vp, vp]
+            L.fdas_zband_work_pairs.argtypes = [vp, i64, i32, f32, f32, i32, i32, i64, i32, i64, vp, vp, vp, vp]
             L.fdas_zband_work_pairs.restype = i32
             L.fdas_static_selftest_wait_timeout.argtypes = [i64, vp]
             L.fdas_static_selftest_wait_timeout.restype = i32
@@ -460,14 +460,17 @@ def zband_work_units(logits, n_windows: int, n_z: int, threshold: float, hop: in
 
 
 def zband_work_pairs(logits, n_windows: int, n_z: int, threshold: float, z_halo: int, hop: int, seg_bins: int,
-                     h: int, n_seg: int, pairs, scratch, stream=None, host_count: bool = True):
+                     h: int, n_seg: int, pairs, scratch, stream=None, host_count: bool = True,
+                     reach_threshold: float | None = None):
     """Pair list s*Z + z into `pairs` (room for n_seg * n_z int32): a template is listed for a
-    segment when one within z_halo of it reaches `threshold` in a block the segment draws on.
-    `scratch`: zband_work_units_scratch_bytes(n_seg, n_z) bytes.  Returns the length
+    segment when one within z_halo of it reaches `threshold` in a block meeting the segment's
+    outputs, or `reach_threshold` (default: threshold) in a block meeting only the inputs beyond
+    them.  `scratch`: zband_work_units_scratch_bytes(n_seg, n_z) bytes.  Returns the length
     (synchronises the stream), or None with host_count=False (the length stays in the scratch,
     zband_work_units_count_ptr(scratch, n_seg))."""
     count = ctypes.c_int64(0)
-    _check(lib().fdas_zband_work_pairs(_ptr(logits), int(n_windows), int(n_z), float(threshold), int(z_halo),
+    reach = float(threshold if reach_threshold is None else reach_threshold)
+    _check(lib().fdas_zband_work_pairs(_ptr(logits), int(n_windows), int(n_z), float(threshold), reach, int(z_halo),
                                        int(hop), int(seg_bins), int(h), int(n_seg), _ptr(pairs), _ptr(scratch),
                                        ctypes.byref(count) if host_count else None, _stream(stream)),
            "fdas_zband_work_pairs")

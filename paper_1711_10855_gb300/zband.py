@@ -191,11 +191,13 @@ class ProposalSearch:
 
     pairs=True (the default at seg_len 2048): the list holds (segment, template) pairs s*Z + z,
     each proposal widened by z_halo templates on both sides, and the pair-list kernel spreads them
-    evenly over the grid's warps.  pairs=False: (segment group, template) units, with per-segment
-    masks when segment_masks is set."""
+    evenly over the grid's warps.  A block next to a segment (meeting only the input bins its
+    templates reach) proposes for it only at reach_threshold or above: only a strong signal there
+    has a response that reaches the segment's outputs.  pairs=False: (segment group, template)
+    units, with per-segment masks when segment_masks is set."""
 
     def __init__(self, net: "fdas.ZBand", plan: "fdas.Plan", device=None, segment_masks: bool = True,
-                 pairs: bool | None = None, z_halo: int = 0):
+                 pairs: bool | None = None, z_halo: int = 0, reach_threshold: float = 0.5):
         import torch
         dev = device or torch.device("cuda")
         if net.window != WINDOW or net.n_out != plan.n_z:
@@ -203,6 +205,7 @@ class ProposalSearch:
         self.net, self.plan = net, plan
         self.pairs = plan.seg_len == 2048 if pairs is None else bool(pairs)
         self.z_halo = int(z_halo)
+        self.reach_threshold = float(reach_threshold)
         self.n_blocks = net.n_blocks(plan.n_bins)
         self.G = plan.group_segments
         self.n_groups = -(-plan.n_seg // self.G)
@@ -222,7 +225,8 @@ class ProposalSearch:
         if self.pairs:
             return fdas.zband_work_pairs(self.logits, self.n_blocks, plan.n_z, threshold, self.z_halo, HOP, plan.valid,
                                          plan.tmpl_len // 2, plan.n_seg, self.units, self.scratch, stream=stream,
-                                         host_count=host_count)
+                                         host_count=host_count,
+                                         reach_threshold=max(float(threshold), self.reach_threshold))
         return fdas.zband_work_units(self.logits, self.n_blocks, plan.n_z, threshold, HOP, self.G * plan.valid,
                                      plan.tmpl_len // 2, self.n_groups, self.units, stream=stream,
                                      scratch=self.scratch, masks=self.masks,

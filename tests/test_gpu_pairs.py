@@ -28,12 +28,16 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("nw,Z,n_seg,z_halo,device_count", [(37, 21, 9, 0, False), (37, 21, 9, 3, True),
-                                                            (600, 300, 190, 2, False), (3200, 5, 1067, 1, True),
-                                                            (50, 12, 16, 12, False)])
-def test_work_pairs_match_oracle(nw, Z, n_seg, z_halo, device_count):
+@pytest.mark.parametrize("nw,Z,n_seg,z_halo,device_count,reach", [(37, 21, 9, 0, False, None),
+                                                                  (37, 21, 9, 3, True, 0.6),
+                                                                  (600, 300, 190, 2, False, 0.9),
+                                                                  (3200, 5, 1067, 1, True, None),
+                                                                  (50, 12, 16, 12, False, 1.0),
+                                                                  (400, 21, 130, 4, False, 0.5)])
+def test_work_pairs_match_oracle(nw, Z, n_seg, z_halo, device_count, reach):
     """Exact lists: Z = 300 spans two 256-template chunks of the writer, 1067 segments more than
-    the scan's 1024 threads, z_halo = Z lists every template of a proposed segment."""
+    the scan's 1024 threads, z_halo = Z lists every template of a proposed segment; margin blocks
+    at the own threshold, at higher reach thresholds, and never (reach 1)."""
     rng = np.random.default_rng(61 + nw + z_halo)
     thr = 0.3
     logits = rng.normal(-3.0, 2.0, (nw, Z)).astype(np.float32)
@@ -42,12 +46,15 @@ def test_work_pairs_match_oracle(nw, Z, n_seg, z_halo, device_count):
     hop, V, h = 512, 1536, 256
     pairs = torch.full((n_seg * Z,), -1, dtype=torch.int32, device="cuda")
     scratch = torch.empty(fdas.zband_work_units_scratch_bytes(n_seg, Z), dtype=torch.uint8, device="cuda")
+    if reach is not None and reach < 1.0:
+        lr = np.log(reach / (1 - reach))
+        logits[np.abs(logits - lr) < 1e-3] += 0.01
     n = fdas.zband_work_pairs(dev(logits), nw, Z, thr, z_halo, hop, V, h, n_seg, pairs, scratch,
-                              host_count=not device_count)
+                              host_count=not device_count, reach_threshold=reach)
     if device_count:
         assert n is None
         n = int(scratch[8 * n_seg:8 * n_seg + 8].view(torch.int64).item())
-    want = oz.work_pairs(logits.astype(np.float64), thr, z_halo, hop, V, h, n_seg)
+    want = oz.work_pairs(logits.astype(np.float64), thr, z_halo, hop, V, h, n_seg, reach_threshold=reach)
     assert n == want.size
     np.testing.assert_array_equal(pairs[:n].cpu().numpy(), want)
 
@@ -56,9 +63,10 @@ def test_work_pairs_rejects_bad_arguments():
     logits = torch.zeros((4, 5), dtype=torch.float32, device="cuda")
     pairs = torch.empty(20, dtype=torch.int32, device="cuda")
     scratch = torch.empty(fdas.zband_work_units_scratch_bytes(4, 5), dtype=torch.uint8, device="cuda")
-    for thr, halo in ((0.0, 0), (1.0, 0), (0.5, -1), (0.5, 6)):
+    for thr, halo, reach in ((0.0, 0, None), (1.0, 0, None), (0.5, -1, None), (0.5, 6, None), (0.5, 0, 0.4),
+                             (0.5, 0, 1.5)):
         with pytest.raises(fdas.FdasError) as e:
-            fdas.zband_work_pairs(logits, 4, 5, thr, halo, 512, 1536, 256, 4, pairs, scratch)
+            fdas.zband_work_pairs(logits, 4, 5, thr, halo, 512, 1536, 256, 4, pairs, scratch, reach_threshold=reach)
         assert e.value.code == fdas.FDAS_ERR_INVALID
     raw = torch.empty(84, dtype=torch.uint8, device="cuda")
     with pytest.raises(fdas.FdasError) as e:   # a pair list 2 bytes off a 4-byte boundary

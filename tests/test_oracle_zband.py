@@ -206,6 +206,23 @@ def test_work_pairs_hand_computed():
     np.testing.assert_array_equal(got, np.arange(5, 25))
 
 
+def test_work_pairs_reach_threshold_hand_computed():
+    """Blocks meeting only a segment's input margin list with the reach threshold."""
+    # blocks of hop 4; 8-bin segments, h = 2: segment s has outputs [8s, 8s + 8) and inputs
+    # [8s - 2, 8s + 10): its own blocks are 2s and 2s + 1, block 2s + 2 ([8s + 8, 8s + 12)) and
+    # block 2s - 1 ([8s - 4, 8s)) meet only its input margin
+    logits = np.full((6, 3), -10.0)
+    logits[2, 0] = 0.0           # p = 0.5: own block of segment 1, margin block of segment 0
+    logits[3, 2] = 3.0           # p = 0.95: own block of segment 1, margin block of segment 2
+    # threshold 0.3 everywhere: segment 0 gets template 0 (margin), segment 1 templates 0 and 2,
+    # segment 2 template 2 (margin)
+    np.testing.assert_array_equal(zband.work_pairs(logits, 0.3, 0, 4, 8, 2, 3), [0, 3, 5, 8])
+    # reach threshold 0.9: the p = 0.5 margin proposal no longer reaches segment 0
+    np.testing.assert_array_equal(zband.work_pairs(logits, 0.3, 0, 4, 8, 2, 3, reach_threshold=0.9), [3, 5, 8])
+    # reach threshold 1: margins never list
+    np.testing.assert_array_equal(zband.work_pairs(logits, 0.3, 0, 4, 8, 2, 3, reach_threshold=1.0), [3, 5])
+
+
 def test_work_pairs_reduce_to_work_units_and_dilate():
     """Halo 0 is the work list with one segment per group; a halo k lists exactly the templates
     within k of a halo-0 pair of the same segment."""
