@@ -56,7 +56,8 @@ struct Layout {
 };
 
 constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)
-constexpr int kSelBlocks = 2048; // grid cap of the median passes
+constexpr int kSelBlocks = 2048; // grid cap of the median's first pass
+constexpr int kSelBlocks12 = 304; // and of its second and third (2 blocks per SM of a GB300)
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
@@ -648,7 +649,6 @@ constexpr int kOffTslot = kOffGroup + 2 * kGroupMisc;
 constexpr int kProposeSmem = kOffTslot + 16;
 constexpr uint32_t kIdesc = fdas::umma_idesc_f16(128, kC);
 constexpr uint32_t kTmemCols = 512;             // 256 columns per group (<= 6 x 32 used)
-constexpr long long kStaggerCycles = 3000;      // start delay of a CTA's second group
 static_assert(kDil1 == 1, "layer 1 is an im2col of adjacent x values");
 static_assert(8 * kDil3 <= 128 && 8 * kDil2 <= 128, "each layer's halo fits in one extra 128-row tile");
 static_assert(2 * kPlaneA1 <= 4 * kPlaneH2, "im2col must fit in the h2 planes");
@@ -830,13 +830,6 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
   const int64_t wstep = 2 * (int64_t)gridDim.x;
   int64_t w = 2 * (int64_t)blockIdx.x + g;
   if (w < p.n_blocks) load_x(w * HOP);
-  // The second group starts ~1.5 us late, so that the two groups' MMA phases interleave with each
-  // other's epilogues instead of starting together (one spectrum of 2^22 bins: 0.387 against
-  // 0.408 ms).  A fixed, clock-bounded delay.
-  if (g == 1) {
-    const long long t0 = clock64();
-    while (clock64() - t0 < kStaggerCycles) __nanosleep(64);
-  }
   for (; w < p.n_blocks; w += wstep) {
 #pragma unroll
     for (int e = 0; e < kXPer; ++e) {
@@ -1036,11 +1029,13 @@ void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* 
   select_init_kernel<<<1, 256, 0, st>>>(sel, n);
   const int64_t blocks = (n + 256 * kSelPer - 1) / (256 * kSelPer);
   const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
+  // passes 1 and 2 flush up to 4096 bins per block: fewer, longer blocks
+  const unsigned grid12 = (unsigned)(blocks < kSelBlocks12 ? blocks : kSelBlocks12);
   select_pass_kernel<0><<<grid, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<0><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<1><<<grid, 256, 0, st>>>(spec, n, sel);
+  select_pass_kernel<1><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<1><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<2><<<grid, 256, 0, st>>>(spec, n, sel);
+  select_pass_kernel<2><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<2><<<1, 256, 0, st>>>(sel, scale);
 }
 }  // namespace
