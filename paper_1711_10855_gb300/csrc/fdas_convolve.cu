@@ -840,42 +840,24 @@ __global__ void __launch_bounds__(256, 1)
 // grid, so a sparse list costs about its share of the full plane's transforms whatever its
 // layout.  The warps are independent: a warp whose range enters a new segment brings it into its
 // shared region (bulk copy of the part inside [0, n), zero fill of the rest) and runs the forward
-// transform (Eq. 3) into its TMEM columns.  A template arrives in two parts: its first PA pairs
-// of every lane (the layout's leading PA*N1 16-byte entries) into a buffer of the warp's own,
-// fetched as soon as the previous transform has read them, i.e. a whole transform ahead; the
-// rest into the region, fetched as soon as the previous transform's exchange tile has been read
-// (both only when the next pair has the same segment).  The warp multiplies, runs the inverse
-// transform and stores |y|^2 for the segment's valid outputs (Section 2, overlap-and-save).  One
-// mbarrier per buffer, at most one copy in flight on each.
-template <class Cfg>
-struct PairLayout {
-  static constexpr int PA = 20;                                    // pairs per lane in the first part
-  static constexpr size_t BYTES_A = (size_t)PA * Cfg::N1 * 16;     // 10 KB
-  static constexpr size_t BYTES_B = (size_t)Cfg::L * 8 - BYTES_A;  // 6 KB
-  static constexpr size_t OFF_A = (size_t)Cfg::W * Cfg::REGION;
-  static constexpr size_t OFF_BAR = OFF_A + (size_t)Cfg::W * BYTES_A;
-  static constexpr size_t SMEM = OFF_BAR + 2 * Cfg::W * 8 + 16;
-  static_assert(PA % 4 == 0 && PA < Cfg::H2 && BYTES_A % 16 == 0 && BYTES_B % 16 == 0, "template split");
-  static_assert(SMEM <= 232448, "shared memory budget of the pair-list kernel");
-};
-
+// transform (Eq. 3) into its TMEM columns; for every pair it brings the template into the same
+// region (bulk copy, issued as soon as the previous transform's exchange tile has been read when
+// the next pair has the same segment), multiplies, runs the inverse transform and stores |y|^2
+// for the segment's valid outputs (Section 2, overlap-and-save).  One mbarrier per warp serves
+// both kinds of copy, at most one of them in flight.
 template <class Cfg, int NV>
 __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairParams p) {
   static_assert(Cfg::F == 1, "one transform per warp");
   constexpr int L = Cfg::L, N1 = Cfg::N1, H2 = Cfg::H2, W = Cfg::W;
-  using PL = PairLayout<Cfg>;
-  constexpr int PA = PL::PA;
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + PL::OFF_BAR);   // [2W]: part A, region
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(wbar + 2 * W);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 2 * W) + 1;
+  uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + (size_t)W * Cfg::REGION);   // [W]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(wbar + W);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + W) + 1;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, k1 = lane;
   float2* myRegion = reinterpret_cast<float2*>(smem + (size_t)warp * Cfg::REGION);
   float4* myXb = reinterpret_cast<float4*>(myRegion);
-  float4* myA = reinterpret_cast<float4*>(smem + PL::OFF_A + (size_t)warp * PL::BYTES_A);
-  uint64_t* barA = &wbar[2 * warp];
-  uint64_t* barB = &wbar[2 * warp + 1];
+  uint64_t* bar = &wbar[warp];
 
   // a list that failed its check (kStatusBadList, set by the preceding check kernel) is not run
   if (*reinterpret_cast<volatile const int*>(p.status) & kStatusBadList) return;
@@ -886,7 +868,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
   const int64_t e0 = (cta0 + warp) * P / NW, e1 = (cta0 + warp + 1) * P / NW;
 
   if (tid == 0) {
-    for (int w = 0; w < 2 * W; ++w) mbar_init(&wbar[w], 1);
+    for (int w = 0; w < W; ++w) mbar_init(&wbar[w], 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -922,39 +904,28 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
   __syncthreads();
   tmem_fence_after_sync();
 
-  // a copy buffer (part A or the region) with its mbarrier, phase and in-flight flag (warp-uniform)
-  struct Buf {
-    uint64_t* bar;
-    uint32_t phase;
-    bool in_flight;
-  };
-  Buf bufA{barA, 0u, false}, bufB{barB, 0u, false};
+  uint32_t phase = 0;
+  bool in_flight = false;   // a copy into this warp's region not yet waited for (warp-uniform)
   // bounded wait for the copy in flight; false after a timeout (the copy stays marked in flight)
-  auto wait_copy = [&](Buf& b) -> bool {
-    const int ok = __all_sync(0xffffffffu, wait_slot(b.bar, b.phase, abort_flag));
+  auto wait_copy = [&]() -> bool {
+    const int ok = __all_sync(0xffffffffu, wait_slot(bar, phase, abort_flag));
     if (!ok) {
       if (lane == 0) report_timeout(p.status, abort_flag);
       return false;
     }
-    b.in_flight = false;
-    b.phase ^= 1u;
+    in_flight = false;
+    phase ^= 1u;
     return true;
   };
-  // `bytes` from src into dst on buffer b (the buffer's earlier generic accesses are ordered
-  // before the copy)
-  auto fetch = [&](Buf& b, void* dst, const void* src, uint32_t bytes) {
+  // template z into the region (its earlier generic accesses are ordered before the copy)
+  auto fetch_template = [&](int z) {
     __syncwarp();
     if (lane == 0) {
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(b.bar, bytes);
-      bulk_g2s(dst, src, bytes, b.bar);
+      mbar_arrive_expect_tx(bar, L * 8);
+      bulk_g2s(myRegion, p.templates + (size_t)z * L, L * 8, bar);
     }
-    b.in_flight = true;
-  };
-  auto fetch_A = [&](int z) { fetch(bufA, myA, p.templates + (size_t)z * L, (uint32_t)PL::BYTES_A); };
-  auto fetch_B = [&](int z) {
-    fetch(bufB, myRegion, reinterpret_cast<const unsigned char*>(p.templates + (size_t)z * L) + PL::BYTES_A,
-          (uint32_t)PL::BYTES_B);
+    in_flight = true;
   };
 
   int64_t cur_s = -1;
@@ -968,10 +939,16 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
       const int64_t x0 = s * (int64_t)p.V - p.h;
       const int64_t c0 = x0 > 0 ? x0 : 0;
       const int64_t c1 = x0 + L < p.n_bins ? x0 + L : p.n_bins;
-      fetch(bufB, myRegion + (c0 - x0), p.spec + c0, (uint32_t)((c1 - c0) * 8));
+      __syncwarp();
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)((c1 - c0) * 8));
+        bulk_g2s(myRegion + (c0 - x0), p.spec + c0, (uint32_t)((c1 - c0) * 8), bar);
+      }
+      in_flight = true;
       for (int i = k1; i < L; i += N1)
         if (x0 + i < c0 || x0 + i >= c1) myRegion[i] = make_float2(0.f, 0.f);
-      if (!wait_copy(bufB)) break;
+      if (!wait_copy()) break;
       __syncwarp();
       // a3: forward FFT of the segment; X pairs (k2 = 2p, 2p+1) go to TMEM
       float xr[16];
@@ -987,26 +964,26 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
           });
       tmem_wait_st();
       cur_s = s;
-      fetch_A(z);
-      fetch_B(z);
+      fetch_template(z);
     }
+    if (!wait_copy()) break;
     // the next pair's template is fetched during this transform when it has the same segment
     int znext = -1;
     if (e + 1 < e1) {
       const int32_t un = __ldg(p.pairs + e + 1);
       if ((int64_t)un / p.Z == s) znext = (int)(un - s * p.Z);
     }
-    // a4: Y = X (TMEM) * T, packed pairs in bit-reversed order: pairs [0, PA) from part A, the
-    // rest from the region
+    // a4: Y = X (TMEM) * T (this warp's region), packed pairs in bit-reversed order
+    const float4* st4 = reinterpret_cast<const float4*>(myRegion);
     cp2 v[H2];
-    auto multiply = [&](auto cc, const float4* t4, auto first) {   // t4 holds pairs from `first` on
-      constexpr int c = decltype(cc)::value, p0 = decltype(first)::value;
+    static_for<H2 / 4>([&](auto cc) {
+      constexpr int c = decltype(cc)::value;
       float x0[16];
       tmem_ld16(x_addr + 16 * c, x0);
       float4 t[4];
       static_for<4>([&](auto qq) {
         constexpr int q = decltype(qq)::value;
-        t[q] = t4[(4 * c + q - p0) * N1 + k1];
+        t[q] = st4[(4 * c + q) * N1 + k1];
       });
       tmem_wait_ld();
       static_for<4>([&](auto qq) {
@@ -1015,14 +992,6 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
         const cp2 x = cp2{make_float2(x0[4 * q], x0[4 * q + 1]), make_float2(x0[4 * q + 2], x0[4 * q + 3])};
         v[bitrev(2 * pp, Cfg::LOG_N2)] = cmul2(x, cp2_from(t[q]));
       });
-    };
-    if (!wait_copy(bufA)) break;
-    static_for<PA / 4>([&](auto cc) { multiply(cc, myA, std::integral_constant<int, 0>{}); });
-    if (znext >= 0) fetch_A(znext);   // part A has been read: the next one arrives a transform ahead
-    if (!wait_copy(bufB)) break;
-    static_for<(H2 - PA) / 4>([&](auto cc) {
-      multiply(std::integral_constant<int, PA / 4 + decltype(cc)::value>{}, reinterpret_cast<const float4*>(myRegion),
-               std::integral_constant<int, PA>{});
     });
     // a5: inverse FFT; a6 + a7: keep n < V inside the spectrum, store |y|^2
     fft_split_pairs<Cfg::N2, +1>(v);
@@ -1044,13 +1013,12 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
           }
         },
         [&]() {
-          if (znext >= 0) fetch_B(znext);
+          if (znext >= 0) fetch_template(znext);
         });
   }
 
-  // copies still in flight after a timeout: wait for them (bounded); always free TMEM
-  if (lane == 0 && bufA.in_flight) (void)mbar_wait(bufA.bar, bufA.phase);
-  if (lane == 0 && bufB.in_flight) (void)mbar_wait(bufB.bar, bufB.phase);
+  // a copy still in flight after a timeout: wait for it (bounded); always free TMEM
+  if (lane == 0 && in_flight) (void)mbar_wait(bar, phase);
   __syncwarp();
   tmem_fence_before_sync();
   __syncthreads();
@@ -1279,7 +1247,8 @@ bool pairs_supported(int L) { return L == 2048; }
 
 template <class Cfg, int NV>
 static cudaError_t launch_pairs_nv(const PairParams& p, int sm_count, cudaStream_t st) {
-  constexpr size_t smem = PairLayout<Cfg>::SMEM;
+  constexpr size_t smem = (size_t)Cfg::W * Cfg::REGION + 128;
+  static_assert(smem <= 232448, "shared memory budget of the pair-list kernel");
   auto kern = fdas_convolve_pairs_kernel<Cfg, NV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
