@@ -834,9 +834,8 @@ def main():
     ap.add_argument("--zband-snr", type=float, nargs=2, default=[5.0, 30.0])
     ap.add_argument("--zband-snr-dist", choices=["uniform", "log-uniform"], default="uniform")
     ap.add_argument("--zband-steps", type=int, default=8000)
-    ap.add_argument("--zband-thresholds", type=float, nargs="+",
-                    default=[0.05, 0.075, 0.1, 0.125, 0.15, 0.2, 0.3, 0.5])
-    ap.add_argument("--zband-halos", type=int, nargs="+", default=[0, 4, 6, 8, 10, 12])
+    ap.add_argument("--zband-thresholds", type=float, nargs="+", default=[0.05, 0.1, 0.15, 0.2, 0.3, 0.5])
+    ap.add_argument("--zband-halos", type=int, nargs="+", default=[0, 4, 8, 12])
     ap.add_argument("--zband-recall", type=float, default=0.97)
     ap.add_argument("--zband-reach", type=float, default=0.5)
     ap.add_argument("--batch-count", type=int, default=256)
