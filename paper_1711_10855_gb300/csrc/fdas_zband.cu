@@ -57,23 +57,25 @@ struct Layout {
 
 constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)
 constexpr int kSelBlocks = 2048; // grid cap of the median's first pass
-constexpr int kSelBlocks12 = 304; // and of its second and third (2 blocks per SM of a GB300)
+constexpr int kSelBlocks1 = 152;  // its second (128 KB of shared memory each: one per SM)
+constexpr int kSelBlocks12 = 304; // and its third (2 blocks per SM of a GB300)
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 // Exact lower median of |A_r|^2 (rank (n-1)/2) by radix selection on the FP32 bit patterns
 // (non-negative floats order as unsigned integers): three passes over the spectrum histogram the
-// top 8 bits (sign and exponent: most values share a few bins, so each warp counts into its own
-// copy), then the next 10 bits of the values matching the digit found so far, then the last 14
-// (few values match 18 bits, so the wide histogram stays sparse); after each pass one block finds
-// the digit holding the rank (a block scan of the histogram).  scale = ln 2 / median.
+// top 8 bits (sign and exponent), then the next 12 bits of the values matching the digit found so
+// far (about a quarter of the values, for noise), then the last 12; after each pass one block
+// finds the digit holding the rank (a block scan of the histogram).  In the first two passes many
+// values share bins, so each warp counts into its own copy of the histogram.
+// scale = ln 2 / median.
 template <int PASS>
 struct SelPass {
-  static constexpr int NB = PASS == 0 ? 256 : (PASS == 1 ? 1024 : 16384);   // bins
-  static constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 14 : 0);
-  static constexpr unsigned MASK = PASS == 0 ? 0xFF000000u : (PASS == 1 ? 0xFFFFC000u : 0xFFFFFFFFu);
-  static constexpr int COPIES = PASS == 0 ? 8 : 1;   // per-warp histograms in pass 0
+  static constexpr int NB = PASS == 0 ? 256 : 4096;   // bins
+  static constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 12 : 0);
+  static constexpr unsigned MASK = PASS == 0 ? 0xFF000000u : (PASS == 1 ? 0xFFFFF000u : 0xFFFFFFFFu);
+  static constexpr int COPIES = PASS == 2 ? 1 : 8;   // per-warp histograms in passes 0 and 1
   static constexpr size_t SMEM = sizeof(unsigned) * COPIES * NB;
 };
 constexpr int kSelPer = 8;   // complex values per thread and pass iteration (four 16-byte loads)
@@ -81,8 +83,8 @@ struct SelectState {
   long long k;                        // rank of the median among the values matching `prefix`
   unsigned prefix, mask;              // bits fixed so far and their mask
   unsigned hist0[SelPass<0>::NB];     // bits 31..24
-  unsigned hist1[SelPass<1>::NB];     // bits 23..14 of the values matching digit 0
-  unsigned hist2[SelPass<2>::NB];     // bits 13..0 of the values matching digits 0 and 1
+  unsigned hist1[SelPass<1>::NB];     // bits 23..12 of the values matching digit 0
+  unsigned hist2[SelPass<2>::NB];     // bits 11..0 of the values matching digits 0 and 1
 };
 
 __device__ __forceinline__ float power_of(const float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
@@ -1035,9 +1037,10 @@ void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* 
   const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
   // passes 1 and 2: fewer, longer blocks, so fewer partial histograms are flushed
   const unsigned grid12 = (unsigned)(blocks < kSelBlocks12 ? blocks : kSelBlocks12);
+  const unsigned grid1 = (unsigned)(blocks < kSelBlocks1 ? blocks : kSelBlocks1);   // 128 KB each
   select_pass_kernel<0><<<grid, 256, SelPass<0>::SMEM, st>>>(spec, n, sel);
   select_digit_kernel<0><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<1><<<grid12, 256, SelPass<1>::SMEM, st>>>(spec, n, sel);
+  select_pass_kernel<1><<<grid1, 256, SelPass<1>::SMEM, st>>>(spec, n, sel);
   select_digit_kernel<1><<<1, 256, 0, st>>>(sel, scale);
   select_pass_kernel<2><<<grid12, 256, SelPass<2>::SMEM, st>>>(spec, n, sel);
   select_digit_kernel<2><<<1, 256, 0, st>>>(sel, scale);
@@ -1074,7 +1077,7 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
           cudaSuccess ||
       cudaFuncSetAttribute(conv_bwd_weight_kernel<kC, true, kDil3>, kSmemAttr, (int)bwd_weight_smem<kC, kDil3>()) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(select_pass_kernel<2>, kSmemAttr, (int)SelPass<2>::SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(select_pass_kernel<1>, kSmemAttr, (int)SelPass<1>::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(propose_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
           cudaSuccess ||
       cudaFuncSetAttribute(propose_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
@@ -1318,8 +1321,8 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
     return FDAS_ERR_INVALID;
   if (reinterpret_cast<uintptr_t>(d_spectrum) & 7u) return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaFuncSetAttribute(select_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SelPass<2>::SMEM) != cudaSuccess)
+  if (cudaFuncSetAttribute(select_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SelPass<1>::SMEM) != cudaSuccess)
     return FDAS_ERR_CUDA;
   SelectState* sel = nullptr;
   float* scale = nullptr;
