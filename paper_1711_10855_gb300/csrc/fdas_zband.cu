@@ -57,52 +57,38 @@ struct Layout {
 
 constexpr float kXCap = 64.f;   // input cap: x_r = min(|A_r|^2 ln 2 / median |A|^2, 64)
 constexpr int kSelBlocks = 2048; // grid cap of the median's first pass
-constexpr int kSelBlocks1 = 152;  // its second (128 KB of shared memory each: one per SM)
-constexpr int kSelBlocks12 = 304; // and its third (2 blocks per SM of a GB300)
+constexpr int kSelBlocks12 = 304; // and of its second and third (2 blocks per SM of a GB300)
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 // Exact lower median of |A_r|^2 (rank (n-1)/2) by radix selection on the FP32 bit patterns
 // (non-negative floats order as unsigned integers): three passes over the spectrum histogram the
-// top 8 bits (sign and exponent), then the next 12 bits of the values matching the digit found so
-// far (about a quarter of the values, for noise), then the last 12; after each pass one block
-// finds the digit holding the rank (a block scan of the histogram).  In the first two passes many
-// values share bins, so each warp counts into its own copy of the histogram.
+// top 8 bits (sign and exponent: most values share a few bins, so each warp counts into its own
+// copy), then the next 12 bits of the values matching the digit found so far, then the last 12;
+// after each pass one block finds the digit holding the rank (a block scan of the histogram).
 // scale = ln 2 / median.
-template <int PASS>
-struct SelPass {
-  static constexpr int NB = PASS == 0 ? 256 : 4096;   // bins
-  static constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 12 : 0);
-  static constexpr unsigned MASK = PASS == 0 ? 0xFF000000u : (PASS == 1 ? 0xFFFFF000u : 0xFFFFFFFFu);
-  static constexpr int COPIES = PASS == 2 ? 1 : 8;   // per-warp histograms in passes 0 and 1
-  static constexpr size_t SMEM = sizeof(unsigned) * COPIES * NB;
-};
+constexpr int kSelBins0 = 256, kSelBins = 4096;
 constexpr int kSelPer = 8;   // complex values per thread and pass iteration (four 16-byte loads)
 struct SelectState {
-  long long k;                        // rank of the median among the values matching `prefix`
-  unsigned prefix, mask;              // bits fixed so far and their mask
-  unsigned hist0[SelPass<0>::NB];     // bits 31..24
-  unsigned hist1[SelPass<1>::NB];     // bits 23..12 of the values matching digit 0
-  unsigned hist2[SelPass<2>::NB];     // bits 11..0 of the values matching digits 0 and 1
+  long long k;                 // rank of the median among the values matching `prefix`
+  unsigned prefix, mask;       // bits fixed so far and their mask
+  unsigned hist0[kSelBins0];   // bits 31..24
+  unsigned hist1[kSelBins];    // bits 23..12 of the values matching digit 0
+  unsigned hist2[kSelBins];    // bits 11..0 of the values matching digits 0 and 1
 };
 
 __device__ __forceinline__ float power_of(const float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
-template <int PASS>
-__device__ __forceinline__ unsigned* sel_hist(SelectState* st) {
-  return PASS == 0 ? st->hist0 : (PASS == 1 ? st->hist1 : st->hist2);
-}
-
-// Histogram of pass PASS over the values whose higher bits equal st->prefix (all values in pass 0).
-// Values are read in 16-byte pairs from the first 16-byte boundary (an 8-byte aligned spectrum's
-// first value is counted on its own); the tail element by element.  Dynamic shared memory:
-// SelPass<PASS>::SMEM bytes.
+// PASS 0: top 8 bits of every value (one histogram per warp, summed at the end); PASS 1, 2: the
+// next 12 bits of the values whose higher bits equal st->prefix.  Values are read in 16-byte pairs from the first 16-byte boundary (an
+// 8-byte aligned spectrum's first value is counted on its own); the tail element by element.
 template <int PASS>
 __global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, int64_t n, SelectState* st) {
-  using SP = SelPass<PASS>;
-  constexpr int NB = SP::NB, SHIFT = SP::SHIFT, COPIES = SP::COPIES;
-  extern __shared__ unsigned h[];
+  constexpr int NB = PASS == 0 ? kSelBins0 : kSelBins;
+  constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 12 : 0);
+  constexpr int COPIES = PASS == 0 ? 8 : 1;   // per-warp histograms in pass 0
+  __shared__ unsigned h[COPIES * NB];
   for (int i = threadIdx.x; i < COPIES * NB; i += 256) h[i] = 0u;
   const unsigned prefix = PASS == 0 ? 0u : st->prefix, mask = PASS == 0 ? 0u : st->mask;
   __syncthreads();
@@ -141,7 +127,7 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, in
     }
   }
   __syncthreads();
-  unsigned* out = sel_hist<PASS>(st);
+  unsigned* out = PASS == 0 ? st->hist0 : (PASS == 1 ? st->hist1 : st->hist2);
   for (int i = threadIdx.x; i < NB; i += 256) {
     unsigned c = 0u;
 #pragma unroll
@@ -155,13 +141,19 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, in
 // holds the rank), appended to st->prefix; after the last digit, scale = ln 2 / median.
 template <int PASS>
 __global__ void __launch_bounds__(256) select_digit_kernel(SelectState* st, float* scale) {
-  using SP = SelPass<PASS>;
-  constexpr int per = SP::NB / 256;
+  constexpr int NB = PASS == 0 ? kSelBins0 : kSelBins;
+  constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 12 : 0);
+  constexpr int per = NB / 256;
   __shared__ long long wsum[8];
-  const unsigned* hist = sel_hist<PASS>(st);
+  const unsigned* hist = PASS == 0 ? st->hist0 : (PASS == 1 ? st->hist1 : st->hist2);
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  unsigned c[per];
   long long own = 0;
-  for (int i = 0; i < per; ++i) own += hist[t * per + i];
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    c[i] = hist[t * per + i];
+    own += c[i];
+  }
   long long inc = own;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -176,16 +168,16 @@ __global__ void __launch_bounds__(256) select_digit_kernel(SelectState* st, floa
   if (k >= excl && k < excl + own) {
     long long r = k - excl;
     int d = t * per;
-    for (int i = 0; i < per - 1; ++i) {
-      const long long c = hist[t * per + i];
-      if (r < c) break;
-      r -= c;
-      ++d;
-    }
-    const unsigned prefix = (PASS == 0 ? 0u : st->prefix) | ((unsigned)d << SP::SHIFT);
+#pragma unroll
+    for (int i = 0; i < per - 1; ++i)
+      if (d == t * per + i && r >= (long long)c[i]) {
+        r -= c[i];
+        ++d;
+      }
+    const unsigned prefix = (PASS == 0 ? 0u : st->prefix) | ((unsigned)d << SHIFT);
     st->k = r;
     st->prefix = prefix;
-    st->mask = SP::MASK;
+    st->mask = PASS == 0 ? 0xFF000000u : (PASS == 1 ? 0xFFFFF000u : 0xFFFFFFFFu);
     if (PASS == 2) {
       const float med = __uint_as_float(prefix);
       *scale = med > 0.f ? 0.69314718055994531f / med : 0.f;
@@ -199,9 +191,11 @@ __global__ void __launch_bounds__(256) select_init_kernel(SelectState* st, int64
     st->prefix = 0u;
     st->mask = 0u;
   }
-  for (int i = threadIdx.x; i < SelPass<0>::NB; i += 256) st->hist0[i] = 0u;
-  for (int i = threadIdx.x; i < SelPass<1>::NB; i += 256) st->hist1[i] = 0u;
-  for (int i = threadIdx.x; i < SelPass<2>::NB; i += 256) st->hist2[i] = 0u;
+  for (int i = threadIdx.x; i < kSelBins0; i += 256) st->hist0[i] = 0u;
+  for (int i = threadIdx.x; i < kSelBins; i += 256) {
+    st->hist1[i] = 0u;
+    st->hist2[i] = 0u;
+  }
 }
 
 __device__ __forceinline__ float power_x(const float2* spec, int64_t n, int64_t r, float scale) {
@@ -1035,14 +1029,13 @@ void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* 
   select_init_kernel<<<1, 256, 0, st>>>(sel, n);
   const int64_t blocks = (n + 256 * kSelPer - 1) / (256 * kSelPer);
   const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
-  // passes 1 and 2: fewer, longer blocks, so fewer partial histograms are flushed
+  // passes 1 and 2 flush up to 4096 bins per block: fewer, longer blocks
   const unsigned grid12 = (unsigned)(blocks < kSelBlocks12 ? blocks : kSelBlocks12);
-  const unsigned grid1 = (unsigned)(blocks < kSelBlocks1 ? blocks : kSelBlocks1);   // 128 KB each
-  select_pass_kernel<0><<<grid, 256, SelPass<0>::SMEM, st>>>(spec, n, sel);
+  select_pass_kernel<0><<<grid, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<0><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<1><<<grid1, 256, SelPass<1>::SMEM, st>>>(spec, n, sel);
+  select_pass_kernel<1><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<1><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<2><<<grid12, 256, SelPass<2>::SMEM, st>>>(spec, n, sel);
+  select_pass_kernel<2><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<2><<<1, 256, 0, st>>>(sel, scale);
 }
 }  // namespace
@@ -1077,7 +1070,6 @@ fdas_zband* fdas_zband_create(int window, int n_out, int max_batch) {
           cudaSuccess ||
       cudaFuncSetAttribute(conv_bwd_weight_kernel<kC, true, kDil3>, kSmemAttr, (int)bwd_weight_smem<kC, kDil3>()) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(select_pass_kernel<1>, kSmemAttr, (int)SelPass<1>::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(propose_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
           cudaSuccess ||
       cudaFuncSetAttribute(propose_kernel<384>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProposeSmem) !=
@@ -1321,9 +1313,6 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
     return FDAS_ERR_INVALID;
   if (reinterpret_cast<uintptr_t>(d_spectrum) & 7u) return FDAS_ERR_ALIGN;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaFuncSetAttribute(select_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SelPass<1>::SMEM) != cudaSuccess)
-    return FDAS_ERR_CUDA;
   SelectState* sel = nullptr;
   float* scale = nullptr;
   if (cudaMallocAsync(&sel, sizeof(SelectState), st) != cudaSuccess) return FDAS_ERR_ALLOC;
