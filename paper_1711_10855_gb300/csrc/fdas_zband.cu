@@ -900,12 +900,7 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
     for (int c = 0; c < kC; ++c) mc[c] = __uint_as_float(sMax[c]);
     for (int j = gt; j < p.Z; j += kGroupThreads) {
       const __half* wl = wl_staged ? sWl + j * kC : p.w + p.oWl + (size_t)j * kC;
-      // four independent FMA chains of 8 channels (the first starting from the bias), then summed
-      static_assert(kC / 8 == 4, "four head chains");
-      float acc[kC / 8];
-#pragma unroll
-      for (int c4 = 0; c4 < kC / 8; ++c4) acc[c4] = 0.f;
-      acc[0] = wl_staged ? sBl[j] : __half2float(p.w[p.obl + j]);
+      float s = wl_staged ? sBl[j] : __half2float(p.w[p.obl + j]);
 #pragma unroll
       for (int c4 = 0; c4 < kC / 8; ++c4) {
         const uint4 u = *reinterpret_cast<const uint4*>(wl + 8 * c4);
@@ -913,11 +908,11 @@ __global__ void __launch_bounds__(256, 1) propose_kernel(const ProposeParams p) 
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const float2 f = __half22float2(h2[e]);
-          acc[c4] = fmaf(f.x, mc[8 * c4 + 2 * e], acc[c4]);
-          acc[c4] = fmaf(f.y, mc[8 * c4 + 2 * e + 1], acc[c4]);
+          s = fmaf(f.x, mc[8 * c4 + 2 * e], s);
+          s = fmaf(f.y, mc[8 * c4 + 2 * e + 1], s);
         }
       }
-      p.logits[w * p.Z + j] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      p.logits[w * p.Z + j] = s;
     }
     group_sync(g);   // sMax and the staging area are reused by the next block
   }
