@@ -316,6 +316,15 @@ def run_batch(args):
     return 0
 
 
+def choose_operating_point(points, target: float) -> dict:
+    """The calibration rule: of the grid points whose recall reaches `target`, the one with the
+    fewest pairs (the first on ties); without any, the highest recall (fewest pairs on ties)."""
+    hits = [p for p in points if p["recall"] >= target]
+    if hits:
+        return min(hits, key=lambda p: p["pair_fraction"])
+    return max(points, key=lambda p: (p["recall"], -p["pair_fraction"]))
+
+
 def run_zband(args):
     """The learned z-band proposal path on the survey plane, measured against the full search.
 
@@ -404,9 +413,7 @@ def run_zband(args):
     calib, n_calib = chirp_spectrum(171110860)
     calib_points = grid(calib)
     del calib
-    hits = [p for p in calib_points if p["recall"] >= args.zband_recall]
-    chosen = (min(hits, key=lambda p: p["pair_fraction"]) if hits
-              else max(calib_points, key=lambda p: (p["recall"], -p["pair_fraction"])))
+    chosen = choose_operating_point(calib_points, args.zband_recall)
     k, thr = chosen["z_halo"], chosen["threshold"]
     dense, n_dense = chirp_spectrum(171110859)
     dense_points = grid(dense)

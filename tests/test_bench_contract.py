@@ -70,3 +70,18 @@ def test_tensor_core_flop_count():
     """Per (segment, template): 3 x (2*32*128*128 + 2*64*64*64) = 4,718,592 tensor flops."""
     assert bench.tc_flops(1, 1) == 4_718_592
     assert abs(bench.tc_flops(2731, 201) / 1e12 - 2.590) < 1e-3
+
+
+def test_operating_point_rule():
+    """Fewest pairs among the points reaching the target; the best recall when none does."""
+    pts = [{"z_halo": 0, "threshold": 0.1, "recall": 0.95, "pair_fraction": 0.05},
+           {"z_halo": 8, "threshold": 0.1, "recall": 0.978, "pair_fraction": 0.18},
+           {"z_halo": 12, "threshold": 0.1, "recall": 0.98, "pair_fraction": 0.22},
+           {"z_halo": 8, "threshold": 0.05, "recall": 0.99, "pair_fraction": 0.35}]
+    assert bench.choose_operating_point(pts, 0.97)["z_halo"] == 8
+    assert bench.choose_operating_point(pts, 0.97)["threshold"] == 0.1
+    assert bench.choose_operating_point(pts, 0.985)["threshold"] == 0.05
+    best = bench.choose_operating_point(pts, 0.999)       # none reaches: the highest recall
+    assert best["recall"] == 0.99
+    tie = pts + [{"z_halo": 4, "threshold": 0.2, "recall": 0.99, "pair_fraction": 0.30}]
+    assert bench.choose_operating_point(tie, 0.999)["pair_fraction"] == 0.30
