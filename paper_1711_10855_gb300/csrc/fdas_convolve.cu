@@ -930,9 +930,10 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
 
   int64_t cur_s = -1;
   for (int64_t e = e0; e < e1; ++e) {
-    const int32_t u = __ldg(p.pairs + e);
-    const int64_t s = u / p.Z;
-    const int z = (int)(u - s * p.Z);
+    const int32_t u = __ldg(p.pairs + e);   // checked: 0 <= u < nseg*Z <= 2^31 - 1
+    const int s32 = u / p.Z;                 // 32-bit division
+    const int64_t s = s32;
+    const int z = u - s32 * p.Z;
     if (s != cur_s) {
       // a2: the segment's window A[sV - h, sV - h + L): bulk copy of its part inside [0, n) (even
       // bounds: n and h are multiples of 4, so every copy is whole 16-byte units), zeros elsewhere
@@ -971,7 +972,7 @@ __global__ void __launch_bounds__(256, 1) fdas_convolve_pairs_kernel(const PairP
     int znext = -1;
     if (e + 1 < e1) {
       const int32_t un = __ldg(p.pairs + e + 1);
-      if ((int64_t)un / p.Z == s) znext = (int)(un - s * p.Z);
+      if (un / p.Z == s32) znext = un - s32 * p.Z;
     }
     // a4: Y = X (TMEM) * T (this warp's region), packed pairs in bit-reversed order
     const float4* st4 = reinterpret_cast<const float4*>(myRegion);
