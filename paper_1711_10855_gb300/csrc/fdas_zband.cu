@@ -65,15 +65,13 @@ __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 // Exact lower median of |A_r|^2 (rank (n-1)/2) by radix selection on the FP32 bit patterns
 // (non-negative floats order as unsigned integers): three passes over the spectrum histogram the
 // top 8 bits (sign and exponent: most values share a few bins, so each warp counts into its own
-// copy), then the next 12 bits of the values matching the digit found so far, which the second
-// pass also copies out (about a quarter of them, for noise), then the last 12 bits of those
-// copies; after each pass one block finds the digit holding the rank (a block scan of the
-// histogram).  scale = ln 2 / median.
+// copy), then the next 12 bits of the values matching the digit found so far, then the last 12;
+// after each pass one block finds the digit holding the rank (a block scan of the histogram).
+// scale = ln 2 / median.
 constexpr int kSelBins0 = 256, kSelBins = 4096;
 constexpr int kSelPer = 8;   // complex values per thread and pass iteration (four 16-byte loads)
 struct SelectState {
   long long k;                 // rank of the median among the values matching `prefix`
-  unsigned long long nvals;    // values the second pass copied out
   unsigned prefix, mask;       // bits fixed so far and their mask
   unsigned hist0[kSelBins0];   // bits 31..24
   unsigned hist1[kSelBins];    // bits 23..12 of the values matching digit 0
@@ -86,8 +84,7 @@ __device__ __forceinline__ float power_of(const float2 a) { return fmaf(a.x, a.x
 // next 12 bits of the values whose higher bits equal st->prefix.  Values are read in 16-byte pairs from the first 16-byte boundary (an
 // 8-byte aligned spectrum's first value is counted on its own); the tail element by element.
 template <int PASS>
-__global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, int64_t n, SelectState* st,
-                                                          unsigned* vals) {
+__global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, int64_t n, SelectState* st) {
   constexpr int NB = PASS == 0 ? kSelBins0 : kSelBins;
   constexpr int SHIFT = PASS == 0 ? 24 : (PASS == 1 ? 12 : 0);
   constexpr int COPIES = PASS == 0 ? 8 : 1;   // per-warp histograms in pass 0
@@ -98,21 +95,14 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, in
   const int lane = threadIdx.x & 31;
   unsigned* hw = h + (COPIES > 1 ? (threadIdx.x >> 5) * NB : 0);
   auto count = [&](float2 a, bool valid) {
-    unsigned bucket = 0xFFFFFFFFu, bits = 0u;
+    unsigned bucket = 0xFFFFFFFFu;
     if (valid) {
-      bits = __float_as_uint(power_of(a));
+      const unsigned bits = __float_as_uint(power_of(a));
       if ((bits & mask) == prefix) bucket = (bits >> SHIFT) & (unsigned)(NB - 1);
     }
     // one shared atomic per distinct bucket of the warp
     const unsigned peers = __match_any_sync(0xffffffffu, bucket);
     if (bucket != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hw[bucket], (unsigned)__popc(peers));
-    if (PASS == 1) {   // copy the matching values out: one global atomic per warp
-      const unsigned take = __ballot_sync(0xffffffffu, bucket != 0xFFFFFFFFu);
-      unsigned long long base = 0ull;
-      if (take && lane == 0) base = atomicAdd(&st->nvals, (unsigned long long)__popc(take));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (bucket != 0xFFFFFFFFu) vals[base + __popc(take & ((1u << lane) - 1u))] = bits;
-    }
   };
   const int off = (reinterpret_cast<uintptr_t>(spec) & 15u) ? 1 : 0;
   if (off && blockIdx.x == 0 && threadIdx.x < 32)
@@ -144,31 +134,6 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const float2* spec, in
     for (int w = 0; w < COPIES; ++w) c += h[w * NB + i];
     if (c) atomicAdd(&out[i], c);
   }
-}
-
-// Third pass over the second pass's copies (their count in st->nvals): the last 12 bits of those
-// whose higher bits equal st->prefix.
-__global__ void __launch_bounds__(256) select_copies_kernel(const unsigned* vals, SelectState* st) {
-  __shared__ unsigned h[kSelBins];
-  for (int i = threadIdx.x; i < kSelBins; i += 256) h[i] = 0u;
-  const unsigned prefix = st->prefix, mask = st->mask;
-  const unsigned long long nv = st->nvals;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const unsigned long long step = (unsigned long long)gridDim.x * 256;
-  for (unsigned long long base = (unsigned long long)blockIdx.x * 256; base < nv; base += step) {
-    const unsigned long long r = base + threadIdx.x;
-    unsigned bucket = 0xFFFFFFFFu;
-    if (r < nv) {
-      const unsigned bits = vals[r];
-      if ((bits & mask) == prefix) bucket = bits & (unsigned)(kSelBins - 1);
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, bucket);
-    if (bucket != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bucket], (unsigned)__popc(peers));
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kSelBins; i += 256)
-    if (h[i]) atomicAdd(&st->hist2[i], h[i]);
 }
 
 // One block of 256 threads: the digit of histogram PASS holding rank st->k (thread t owns the
@@ -223,7 +188,6 @@ __global__ void __launch_bounds__(256) select_digit_kernel(SelectState* st, floa
 __global__ void __launch_bounds__(256) select_init_kernel(SelectState* st, int64_t n) {
   if (threadIdx.x == 0) {
     st->k = (n - 1) / 2;
-    st->nvals = 0ull;
     st->prefix = 0u;
     st->mask = 0u;
   }
@@ -985,8 +949,6 @@ struct fdas_zband {
   float* loss_part = nullptr; // per-warp loss partials [ceil(B*Z / 32)]
   float* wpart = nullptr;    // weight-gradient partials [B * Wd/128][C*C*9 + C]
   SelectState* sel = nullptr; // median selection state
-  unsigned* vals = nullptr;   // the median's second-pass copies (room for vals_cap values)
-  int64_t vals_cap = 0;
   float* scale = nullptr;    // ln 2 / median |A|^2
   int* status = nullptr;     // bit 0: a bounded wait of the inference kernel gave up
   int step = 0;
@@ -1007,7 +969,7 @@ namespace {
 void free_zband(fdas_zband* z) {
   void* ptrs[] = {z->p,      z->ph,  z->g,      z->m,    z->v,         z->a1,     z->a2,
                   z->a3,     z->d1,  z->d2,     z->pooled, z->arg,    z->logits, z->dlog,
-                  z->loss,   z->loss_part, z->wpart, z->sel, z->scale, z->status, z->vals};
+                  z->loss,   z->loss_part, z->wpart, z->sel, z->scale, z->status};
   for (void* q : ptrs) cudaFree(q);
   if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
   if (z->graph) cudaGraphDestroy(z->graph);
@@ -1063,19 +1025,17 @@ cudaError_t forward(fdas_zband* z, const float* in, int B, bool half_weights, cu
 }
 
 // scale = ln 2 / median |A|^2 into `scale`: seven launches.
-// vals: room for n unsigned (the second pass's copies).
-void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* scale, unsigned* vals,
-                        cudaStream_t st) {
+void launch_power_scale(const float2* spec, int64_t n, SelectState* sel, float* scale, cudaStream_t st) {
   select_init_kernel<<<1, 256, 0, st>>>(sel, n);
   const int64_t blocks = (n + 256 * kSelPer - 1) / (256 * kSelPer);
   const unsigned grid = (unsigned)(blocks < kSelBlocks ? blocks : kSelBlocks);
-  // the second pass flushes up to 4096 bins per block: fewer, longer blocks
+  // passes 1 and 2 flush up to 4096 bins per block: fewer, longer blocks
   const unsigned grid12 = (unsigned)(blocks < kSelBlocks12 ? blocks : kSelBlocks12);
-  select_pass_kernel<0><<<grid, 256, 0, st>>>(spec, n, sel, nullptr);
+  select_pass_kernel<0><<<grid, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<0><<<1, 256, 0, st>>>(sel, scale);
-  select_pass_kernel<1><<<grid12, 256, 0, st>>>(spec, n, sel, vals);
+  select_pass_kernel<1><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<1><<<1, 256, 0, st>>>(sel, scale);
-  select_copies_kernel<<<grid12, 256, 0, st>>>(vals, sel);
+  select_pass_kernel<2><<<grid12, 256, 0, st>>>(spec, n, sel);
   select_digit_kernel<2><<<1, 256, 0, st>>>(sel, scale);
 }
 }  // namespace
@@ -1259,7 +1219,7 @@ static cudaError_t launch_propose(fdas_zband* z, const float* d_spectrum, int64_
                                   cudaStream_t st) {
   const int hop = z->Wd / 2;
   const int64_t nb = (n_bins + hop - 1) / hop;
-  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->sel, z->scale, z->vals, st);
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, z->sel, z->scale, st);
   ProposeParams q;
   q.spec = reinterpret_cast<const float2*>(d_spectrum);
   q.n = n_bins;
@@ -1299,22 +1259,6 @@ int fdas_zband_propose(fdas_zband* z, const float* d_spectrum, int64_t n_bins, f
   // eight launches replayed as one graph: captured again when the spectrum, its length or the
   // logits buffer change (the weights are read through fixed pointers, so training needs none)
   if (!(z->graph_exec && z->cap_spec == d_spectrum && z->cap_n == n_bins && z->cap_logits == d_logits)) {
-    // the median's copy buffer grows to this spectrum's length (after the net's last work)
-    if (n_bins > z->vals_cap) {
-      if (cudaEventSynchronize(z->done) != cudaSuccess) return FDAS_ERR_CUDA;
-      cudaFree(z->vals);
-      z->vals = nullptr;
-      z->vals_cap = 0;
-      if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
-      if (z->graph) cudaGraphDestroy(z->graph);
-      z->graph_exec = nullptr;
-      z->graph = nullptr;
-      if (cudaMalloc(&z->vals, sizeof(unsigned) * (size_t)n_bins) != cudaSuccess) {
-        cudaGetLastError();
-        return FDAS_ERR_ALLOC;
-      }
-      z->vals_cap = n_bins;
-    }
     if (z->graph_exec) cudaGraphExecDestroy(z->graph_exec);
     if (z->graph) cudaGraphDestroy(z->graph);
     z->graph_exec = nullptr;
@@ -1371,22 +1315,17 @@ int fdas_zband_spectrum_windows(const float* d_spectrum, int64_t n_bins, int win
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SelectState* sel = nullptr;
   float* scale = nullptr;
-  unsigned* vals = nullptr;
   if (cudaMallocAsync(&sel, sizeof(SelectState), st) != cudaSuccess) return FDAS_ERR_ALLOC;
-  if (cudaMallocAsync(&scale, 4, st) != cudaSuccess ||
-      cudaMallocAsync(&vals, sizeof(unsigned) * (size_t)n_bins, st) != cudaSuccess) {
-    cudaGetLastError();
+  if (cudaMallocAsync(&scale, 4, st) != cudaSuccess) {
     cudaFreeAsync(sel, st);
-    if (scale) cudaFreeAsync(scale, st);
     return FDAS_ERR_ALLOC;
   }
-  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, sel, scale, vals, st);
+  launch_power_scale(reinterpret_cast<const float2*>(d_spectrum), n_bins, sel, scale, st);
   spectrum_windows_kernel<<<(unsigned)n_windows, 256, 0, st>>>(reinterpret_cast<const float2*>(d_spectrum), n_bins,
                                                                scale, window, hop, d_windows);
   const int rc = cudaGetLastError() == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
   cudaFreeAsync(sel, st);
   cudaFreeAsync(scale, st);
-  cudaFreeAsync(vals, st);
   return rc;
 }
 
