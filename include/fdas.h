@@ -354,7 +354,7 @@ int fdas_zband_predict(fdas_zband* net, const float* d_windows, int batch, int h
  * the network's output for window w (the same value fdas_zband_predict gives for that window,
  * up to FP16 rounding of the activations).  Requires H = W/2 to be a multiple of 128 and at
  * most 512 (W = 512, 768 or 1024).  Asynchronous; uses the net's scratch, so calls on one net
- * must not overlap.  Its six launches (exact median, inference) run as a CUDA graph: the first
+ * must not overlap.  Its eight launches (exact median, inference) run as a CUDA graph: the first
  * call with a given (d_spectrum, n_bins, d_logits) captures and instantiates it (driver
  * allocations), later calls with the same arguments replay it with no allocation; new weights
  * need no new capture.  A bounded device wait that gives up is reported by fdas_zband_check. */
